@@ -1,0 +1,160 @@
+/*
+ * lrei.h -- C ABI of the GB300 low-rank eigenmode-integration (LREI) stepper.
+ *
+ * The library time-steps the quantum Landau-Lifshitz (q-LL) and quantum
+ * Landau-Lifshitz-Gilbert (q-LLG) equations for a spin-1/2 system of n spins
+ * (N = 2^n) with a density matrix kept in factored form rho = V Lambda_0 V^*,
+ * V an N x r matrix with orthonormal columns and Lambda_0 the fixed spectrum
+ * (paper: Sec. 3.1 eq. partial-eigendecom and Sec. 3.6 "Memory-efficient
+ * representation").  hbar = 1 throughout.
+ *
+ * Conventions shared by every entry point
+ *  - Complex numbers are stored as interleaved (re, im) pairs: dtype
+ *    LREI_C128 = two doubles, LREI_C64 = two floats.
+ *  - An N x r factor is stored row-major: element (b, c) at offset b*ld + c,
+ *    ld >= r; the r columns of one basis state b are contiguous.
+ *  - Basis index b: site i (0-based) is Kronecker factor i from the left
+ *    (Sec. 3.6 eq. spin_op), i.e. bit n-1-i of b; bit value 0 = spin up.
+ *  - "_dev" pointers are CUDA device pointers; "_host" pointers are host
+ *    memory.  The library copies every input it keeps; it never frees or
+ *    retains caller memory.
+ *  - Every call returns an int: LREI_OK (0) or a negative lrei_status code.
+ *    No C++ exception crosses the ABI.  lrei_error_string() describes a code.
+ *  - All work is enqueued on the stream given to lrei_create (NULL = legacy
+ *    default stream).  Calls that return host data synchronise that stream.
+ *  - One context must not be used from two threads at once.
+ */
+#ifndef LREI_H
+#define LREI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrei_ctx lrei_ctx; /* opaque; owns all device memory it uses */
+
+typedef enum {
+  LREI_OK = 0,
+  LREI_ERR_ARG = -1,         /* invalid argument (sizes, ranges, NULL) */
+  LREI_ERR_UNSUPPORTED = -2, /* valid physics outside this build (B_x, B_y != 0) */
+  LREI_ERR_NONFINITE = -3,   /* NaN/Inf in an input or produced by a step */
+  LREI_ERR_TRACE = -4,       /* Lambda not >= 0 or |sum(Lambda) - 1| > 1e-12 */
+  LREI_ERR_RANK = -5,        /* V rank-deficient */
+  LREI_ERR_EIG_NOCONV = -6,  /* small eigensolver did not converge */
+  LREI_ERR_OOM = -7,         /* device allocation failed */
+  LREI_ERR_CUDA = -8,        /* other CUDA runtime error */
+  LREI_ERR_STATE = -9,       /* call out of order (e.g. step before set_state) */
+  LREI_ERR_TIMEOUT = -10     /* a bounded device-side wait ran out */
+} lrei_status;
+
+typedef enum { LREI_QLL = 0, LREI_QLLG = 1 } lrei_model;
+
+typedef enum {
+  LREI_RK1 = 0, LREI_RK2 = 1, LREI_RK3 = 2, LREI_RK4 = 3,
+  LREI_AB2 = 4, LREI_AB3 = 5, LREI_AB4 = 6
+} lrei_scheme;
+
+/* Arithmetic of the N-length (bulk) work.  Small r x r / k x k solves are
+ * FP64 in every mode. */
+typedef enum {
+  LREI_FP64 = 0,      /* complex128 storage and arithmetic */
+  LREI_MIXED_C64 = 1  /* complex64 storage and FP32 arithmetic, FP64 small solves */
+} lrei_precision;
+
+typedef enum { LREI_C128 = 0, LREI_C64 = 1 } lrei_dtype;
+
+/* Exchange bonds of the spin Hamiltonian, eq. H1 without DMI: each bond (i, j)
+ * contributes 2*jxy*(S^x_i S^x_j + S^y_i S^y_j) + 2*jz*S^z_i S^z_j, i.e. a
+ * pair-flip amplitude jxy and a diagonal +-jz/2.  Host arrays, copied. */
+typedef struct {
+  int nbonds;
+  const int *site_i, *site_j;
+  const double *jxy, *jz;
+} lrei_bonds;
+
+/* Observables of the current state (Sec. 3.6 eq. measuerA). */
+typedef struct {
+  double t;          /* simulated time */
+  double energy;     /* Tr(rho H) */
+  double mx, my, mz; /* Tr(rho M_v), M_v = (1/n) sum_i S_i^v */
+  double purity;     /* Tr((Lambda_0 V^*V)^2) of the stored factor */
+  double trace;      /* Tr(Lambda_0 V^*V) of the stored factor */
+  double orth_err;   /* max |V^*V - I| of the stored factor */
+  double herm_err;   /* max |G - G^*| / max|G|, G = V^*HV */
+  double comm_norm;  /* ||[rho, H]||_F */
+  int r;             /* current rank */
+  double ritz[64];   /* r largest eigenvalues of the last unprojected rho_{k+1} */
+  double lambda0[64];/* the conserved spectrum, decreasing */
+} lrei_obs;
+
+/* Create a context for n spins (1 <= n <= 26).
+ *   J       exchange bonds (eq. H1), site indices in [0, n)
+ *   B       Zeeman field (B_x, B_y, B_z): H_Z = B . sum_i S_i; B_x = B_y = 0
+ *           in this build (else LREI_ERR_UNSUPPORTED)
+ *   lambda  damping kappa >= 0 of eqs. q-LL / q-LLG
+ *   r_max   largest rank the context will hold (1..32)
+ *   cuda_stream  cudaStream_t (may be NULL)
+ * Allocates all device memory the context needs for ranks <= r_max. */
+int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda,
+                lrei_model model, lrei_precision prec, int r_max,
+                void *cuda_stream, lrei_ctx **out);
+
+/* Set rho_0 = V diag(Lambda) V^* from any full-column-rank V (N x r, device,
+ * row stride ld, dtype LREI_C128 or LREI_C64) and Lambda (host, r values >= 0
+ * summing to 1).  The library orthonormalises V (Cholesky QR), diagonalises
+ * R Lambda R^* and stores (V~, Lambda_0) with Lambda_0 decreasing (Sec. 3.1,
+ * Sec. 3.7 "Given the sparse initial density matrix ...").  Resets t to 0 and
+ * clears any multistep history. */
+int lrei_set_state(lrei_ctx *ctx, const void *V_dev, int r, int ld, int dtype,
+                   const double *Lambda_host);
+
+/* Copy the current factor out (N x r, row-major, ld = r, dtype of the
+ * context's precision: C128 for LREI_FP64, C64 for LREI_MIXED_C64), the
+ * spectrum Lambda_0 (r doubles) and t.  Any pointer may be NULL. */
+int lrei_get_state(lrei_ctx *ctx, void *V_dev_out, double *Lambda_host_out,
+                   double *t_out);
+
+/* Advance nsteps fixed steps of size dt with an LREI-RK (Sec. 3.7) or LREI-AB
+ * (Sec. 3.8) scheme.  AB_m takes its first m-1 steps with RK4 and keeps its
+ * history across calls while scheme and dt stay the same. */
+int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
+
+/* Advance to t_end with RK4 and an adaptive step: controller 0 = the plain
+ * rule (spectral-drift estimate, step doubling as judge), 1 = the learned
+ * controller (falls back to the plain rule when its prediction is judged
+ * wrong).  tol bounds the relative local error per step. */
+int lrei_step_adaptive(lrei_ctx *ctx, double t_end, double tol, int controller);
+
+/* Compute observables of the current state into a host struct (syncs). */
+int lrei_observables(lrei_ctx *ctx, lrei_obs *out);
+
+/* Free the context and all device memory it owns. */
+int lrei_destroy(lrei_ctx *ctx);
+
+const char *lrei_error_string(int code);
+
+/* ---- entry points exposing single steps of the hot path ---------------- */
+
+/* Y = H V for an N x r block (matrix-free action of eq. H1 on basis
+ * bitstrings; Sec. 3.3 "sparsity of H").  V_dev, Y_dev device, row-major with
+ * ld = r, dtype must match the context's precision.  V_dev != Y_dev. */
+int lrei_apply_h(lrei_ctx *ctx, const void *V_dev, void *Y_dev, int r);
+
+/* Low-rank right-hand side at the current state: f(rho) = Z V^* + V W^*
+ * (Sec. 3.5 eq. q-LLG-low-rank; q-LL blocks of Sec. 4).  Writes Z and W
+ * (N x r each, device, ld = r, the context's dtype) and, if G_host is not
+ * NULL, G = V^*HV (r x r complex, column-major, 2*r*r doubles).
+ * complement: 0 = projector form W = (I - VV^*) H V diag(conj c),
+ *             1 = Householder reflectors of V applied as in Sec. 3.4
+ *                 (compact WY form). */
+int lrei_rhs(lrei_ctx *ctx, void *Z_dev, void *W_dev, double *G_host,
+             int complement);
+
+/* Number of kernels this library launched on the context's stream since the
+ * last call (resets the counter). */
+long long lrei_kernel_launches(lrei_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LREI_H */

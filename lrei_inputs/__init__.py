@@ -1,0 +1,172 @@
+"""Seeded synthetic inputs shared by the CPU oracle and the CUDA path.
+
+This module holds no arithmetic of the LREI method itself: it only draws
+random numbers and lays out named basis states, bond lists and the five
+workload recipes.  Both sides of every parity test receive the same arrays
+from here.
+
+Conventions (the paper's spin-1/2 Kronecker order, Sec. 3.6, eq. spin_op):
+  * site i (0-based) is Kronecker factor i counted from the left, i.e. bit
+    (n-1-i) of the basis index b (site 0 is the most significant bit);
+  * bit value 0 is spin up (S^z = +1/2), 1 is spin down.
+
+Seed recipe: workload c, trajectory t uses numpy Generator(PCG64(1000*c + t));
+draw order is bond anisotropies, then the initial factor V, then Lambda.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+__all__ = [
+    "Bonds", "chain_bonds", "haar_orthonormal", "dirichlet_spectrum",
+    "basis_state", "af1_state", "af2_state", "ghz_state", "w_state",
+    "Workload", "workload", "rng_for",
+]
+
+
+@dataclasses.dataclass
+class Bonds:
+    """Exchange bonds (i, j) with coupling Jxy (S^+S^- part) and Jz (S^zS^z part)."""
+    site_i: np.ndarray  # int32
+    site_j: np.ndarray  # int32
+    jxy: np.ndarray     # float64
+    jz: np.ndarray      # float64
+
+    def __len__(self):
+        return int(self.site_i.shape[0])
+
+
+def rng_for(config: int, traj: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(1000 * config + traj))
+
+
+def chain_bonds(n: int, periodic: bool, J: float = 1.0, aniso: np.ndarray | None = None) -> Bonds:
+    """Nearest-neighbour chain bonds; Jz = J + aniso[b] when an anisotropy list is given."""
+    m = n if (periodic and n > 2) else n - 1
+    si = np.arange(m, dtype=np.int32)
+    sj = ((si + 1) % n).astype(np.int32)
+    jxy = np.full(m, float(J))
+    jz = np.full(m, float(J))
+    if aniso is not None:
+        jz = jz + np.asarray(aniso, dtype=np.float64)[:m]
+    return Bonds(si, sj, jxy, jz)
+
+
+def haar_orthonormal(N: int, r: int, rng: np.random.Generator) -> np.ndarray:
+    """N x r matrix with Haar-distributed orthonormal columns (complex Ginibre + QR, Mezzadri 2007)."""
+    G = (rng.standard_normal((N, r)) + 1j * rng.standard_normal((N, r))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(G)
+    d = np.diag(R)
+    ph = d / np.abs(d)
+    return np.ascontiguousarray(Q * ph[None, :])
+
+
+def dirichlet_spectrum(r: int, rng: np.random.Generator, alpha: float = 1.0) -> np.ndarray:
+    """Dirichlet(alpha) weights sorted in decreasing order (a trace-one positive spectrum)."""
+    lam = rng.dirichlet(np.full(r, alpha))
+    return np.sort(lam)[::-1].copy()
+
+
+def basis_state(n: int, index: int) -> np.ndarray:
+    v = np.zeros(1 << n, dtype=np.complex128)
+    v[index] = 1.0
+    return v
+
+
+def _alternating(n: int, first: int) -> int:
+    # bit string of length n read from site 0 (MSB) to site n-1 (LSB)
+    idx = 0
+    for i in range(n):
+        bit = (first + i) & 1
+        idx = (idx << 1) | bit
+    return idx
+
+
+def af1_state(n: int) -> np.ndarray:
+    """|AF1>: the single basis state whose bit string is 0101... (site 0 first)."""
+    return basis_state(n, _alternating(n, 0))
+
+
+def af2_state(n: int) -> np.ndarray:
+    """|AF2>: the single basis state whose bit string is 1010... (site 0 first)."""
+    return basis_state(n, _alternating(n, 1))
+
+
+def ghz_state(n: int) -> np.ndarray:
+    v = np.zeros(1 << n, dtype=np.complex128)
+    v[0] = v[(1 << n) - 1] = 1.0 / np.sqrt(2.0)
+    return v
+
+
+def w_state(n: int) -> np.ndarray:
+    v = np.zeros(1 << n, dtype=np.complex128)
+    for i in range(n):
+        v[1 << (n - 1 - i)] = 1.0 / np.sqrt(n)
+    return v
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    n: int
+    r: int
+    bonds: Bonds
+    B: tuple
+    kappa: float
+    model: str          # "qll" | "qllg"
+    scheme: str         # "rk4", "ab3", ...
+    dt: float
+    steps: int
+    V: np.ndarray | None = None
+    lam: np.ndarray | None = None
+
+
+def workload(config: int, traj: int = 0, *, n: int | None = None, r: int | None = None,
+             kappa: float | None = None, model: str | None = None, scheme: str | None = None,
+             with_state: bool = True) -> Workload:
+    """The synthetic workloads.
+
+    1: open chain n=8, r=4, J=1, B_z=0.5, kappa=0.1, q-LL, RK4, dt=0.01, 1000 steps.
+    2: periodic chain n=16, r=8, Jxy=1, Jz=1+U[-0.2,0.2] per bond, B_z=1, dt=0.005, 500 steps.
+    3: open chain n=20, r=16, J=1, B_z=0.5, kappa=0.1, RK4, dt=0.01, 100 steps.
+    4: open chains n in U{10..18}, r in U{2..16}, kappa log-uniform in [1e-3, 1], RK4, dt=0.01, 200 steps.
+    5: open chain n=22, r=32, kappa=0.05, J=1, B_z=0.5, 50 steps (controller evaluation).
+    Keyword overrides let tests shrink a workload while keeping its recipe.
+    """
+    rng = rng_for(config, traj)
+    if config == 1:
+        nn, rr, bonds, B, kap, mdl, sch, dt, steps = 8, 4, None, (0.0, 0.0, 0.5), 0.1, "qll", "rk4", 0.01, 1000
+        nn = n or nn
+        bonds = chain_bonds(nn, periodic=False)
+    elif config == 2:
+        nn = n or 16
+        m = nn if nn > 2 else nn - 1
+        aniso = rng.uniform(-0.2, 0.2, size=m)
+        bonds = chain_bonds(nn, periodic=True, aniso=aniso)
+        rr, B, kap, mdl, sch, dt, steps = 8, (0.0, 0.0, 1.0), 0.1, "qll", "rk4", 0.005, 500
+    elif config == 3:
+        nn = n or 20
+        bonds = chain_bonds(nn, periodic=False)
+        rr, B, kap, mdl, sch, dt, steps = 16, (0.0, 0.0, 0.5), 0.1, "qll", "rk4", 0.01, 100
+    elif config == 4:
+        nn = n or int(rng.integers(10, 19))
+        rr = r or int(rng.integers(2, 17))
+        kap = kappa if kappa is not None else float(10.0 ** rng.uniform(-3.0, 0.0))
+        bonds = chain_bonds(nn, periodic=False)
+        B, mdl, sch, dt, steps = (0.0, 0.0, 0.5), "qll", "rk4", 0.01, 200
+    elif config == 5:
+        nn = n or 22
+        bonds = chain_bonds(nn, periodic=False)
+        rr, B, kap, mdl, sch, dt, steps = 32, (0.0, 0.0, 0.5), 0.05, "qll", "rk4", 0.01, 50
+    else:
+        raise ValueError(f"unknown workload {config}")
+    rr = r or rr
+    kap = kappa if kappa is not None else kap
+    mdl = model or mdl
+    sch = scheme or sch
+    w = Workload(f"cfg{config}", nn, rr, bonds, B, kap, mdl, sch, dt, steps)
+    if with_state:
+        w.V = haar_orthonormal(1 << nn, rr, rng)
+        w.lam = dirichlet_spectrum(rr, rng)
+    return w

@@ -1,0 +1,69 @@
+"""Dense spin operators and the spin Hamiltonian (oracle; test infrastructure only).
+
+Paper: Sec. 3.6 eq. spin_op (S_i^v as a Kronecker product with sigma_v/2 in
+factor i) and Sec. 5 eq. H1 (exchange + Zeeman Hamiltonian).  hbar = 1.
+
+Readings used here (each listed in the design doc):
+  * the exchange sum of eq. H1 runs once over each listed bond (i, j); an
+    XXZ bond carries 2*Jxy*(S^x S^x + S^y S^y) + 2*Jz*S^z S^z, which for
+    Jxy = Jz = J is the paper's 2J S_i . S_j;
+  * the Zeeman term is B . sum_i S_i with B the field in energy units
+    (B = g mu_B b of eq. H1 with hbar = 1; the sign of -mu b . S with
+    mu = -mu_B g / hbar is +g mu_B b . S);
+  * site i is Kronecker factor i from the left, so site 0 is the most
+    significant bit of the basis index; bit 0 means spin up.
+
+The matrices are built from Kronecker products on purpose: this is a
+different mechanism from the GPU kernels' bit arithmetic, so agreement also
+pins the bit order.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+SIGMA_X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+SIGMA_Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+SIGMA_Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+PAULI = {"x": SIGMA_X, "y": SIGMA_Y, "z": SIGMA_Z}
+
+
+def spin_op(v: str, i: int, n: int, sparse: bool = False):
+    """S_i^v = I x ... x (1/2) sigma_v x ... x I with sigma_v in Kronecker factor i (eq. spin_op)."""
+    op = 0.5 * PAULI[v]
+    if sparse:
+        left = sp.identity(1 << i, dtype=np.complex128, format="csr")
+        right = sp.identity(1 << (n - i - 1), dtype=np.complex128, format="csr")
+        return sp.kron(sp.kron(left, sp.csr_matrix(op)), right, format="csr")
+    return np.kron(np.kron(np.eye(1 << i), op), np.eye(1 << (n - i - 1)))
+
+
+def magnetization_op(v: str, n: int, sparse: bool = False):
+    """M_v = (1/n) sum_i S_i^v (Sec. 3.6)."""
+    M = None
+    for i in range(n):
+        t = spin_op(v, i, n, sparse)
+        M = t if M is None else M + t
+    return M / n
+
+
+def hamiltonian(n: int, bonds, B=(0.0, 0.0, 0.0), sparse: bool = False):
+    """Spin Hamiltonian of eq. H1 without DMI: sum over bonds of the XXZ exchange plus B . sum_i S_i."""
+    N = 1 << n
+    H = sp.csr_matrix((N, N), dtype=np.complex128) if sparse else np.zeros((N, N), dtype=np.complex128)
+    for b in range(len(bonds)):
+        i, j = int(bonds.site_i[b]), int(bonds.site_j[b])
+        jxy, jz = float(bonds.jxy[b]), float(bonds.jz[b])
+        for v, c in (("x", jxy), ("y", jxy), ("z", jz)):
+            if c != 0.0:
+                H = H + 2.0 * c * (spin_op(v, i, n, sparse) @ spin_op(v, j, n, sparse))
+    for v, c in zip("xyz", B):
+        if c != 0.0:
+            for i in range(n):
+                H = H + c * spin_op(v, i, n, sparse)
+    return H
+
+
+def expectation(A, rho) -> float:
+    """<A> = Tr(A rho) (Sec. 3.6)."""
+    return float(np.real(np.trace(A @ rho)))
