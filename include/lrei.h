@@ -150,6 +150,11 @@ int lrei_apply_h(lrei_ctx *ctx, const void *V_dev, void *Y_dev, int r);
 int lrei_rhs(lrei_ctx *ctx, void *Z_dev, void *W_dev, double *G_host,
              int complement);
 
+/* Raw device status bits of the last step / set_state call (diagnostics):
+ * 1 non-finite, 2 small eigensolver sweep limit, 4 rank-deficient factor,
+ * 8 bounded wait ran out, 16 trace, 32 eigenpair residual above tolerance. */
+int lrei_last_status(lrei_ctx *ctx);
+
 /* Number of kernels this library launched on the context's stream since the
  * last call (resets the counter). */
 long long lrei_kernel_launches(lrei_ctx *ctx);

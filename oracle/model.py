@@ -67,3 +67,33 @@ def hamiltonian(n: int, bonds, B=(0.0, 0.0, 0.0), sparse: bool = False):
 def expectation(A, rho) -> float:
     """<A> = Tr(A rho) (Sec. 3.6)."""
     return float(np.real(np.trace(A @ rho)))
+
+
+def hamiltonian_row(n: int, bonds, B, b: int) -> np.ndarray:
+    """Row b of the Hamiltonian of eq. H1, as a dense length-2^n vector.
+
+    Row b of a Kronecker product is the Kronecker product of the factors' rows
+    (row bit of factor i = bit n-1-i of b), so each term's row is built from
+    2-vectors.  Used to check single output rows at sizes where H cannot be formed.
+    """
+    bits = [(b >> (n - 1 - i)) & 1 for i in range(n)]
+    N = 1 << n
+    row = np.zeros(N, dtype=np.complex128)
+
+    def term_row(ops):
+        v = np.ones(1, dtype=np.complex128)
+        for i in range(n):
+            f = ops.get(i)
+            v = np.kron(v, (f[bits[i], :] if f is not None else np.eye(2)[bits[i], :]))
+        return v
+
+    for k in range(len(bonds)):
+        i, j = int(bonds.site_i[k]), int(bonds.site_j[k])
+        for v_, c in (("x", float(bonds.jxy[k])), ("y", float(bonds.jxy[k])), ("z", float(bonds.jz[k]))):
+            if c != 0.0:
+                row += 2.0 * c * term_row({i: 0.5 * PAULI[v_], j: 0.5 * PAULI[v_]})
+    for v_, c in zip("xyz", B):
+        if c != 0.0:
+            for i in range(n):
+                row += c * term_row({i: 0.5 * PAULI[v_]})
+    return row

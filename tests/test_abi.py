@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/lrei.h declares (no GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lrei.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lrei_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2508_21200_gb300 import build
+    try:
+        return build.ensure_built()
+    except (RuntimeError, FileNotFoundError) as e:  # no nvcc in this environment
+        pytest.skip(f"cannot build: {e}")
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("lrei_create", "lrei_set_state", "lrei_step", "lrei_observables", "lrei_destroy"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    for s in declared_symbols():
+        assert re.search(rf"\bT {s}$", out, flags=re.M), s
+
+
+def test_error_strings_without_gpu(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.lrei_error_string.restype = ctypes.c_char_p
+    assert lib.lrei_error_string(0) == b"ok"
+    assert b"argument" in lib.lrei_error_string(-1)
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    h = ctypes.c_void_p()
+    B = (ctypes.c_double * 3)(0.0, 0.0, 0.5)
+    assert lib.lrei_create(0, None, B, ctypes.c_double(0.1), 0, 0, 4, None, ctypes.byref(h)) == -1   # n < 1
+    assert lib.lrei_create(8, None, B, ctypes.c_double(-1.0), 0, 0, 4, None, ctypes.byref(h)) == -1  # kappa < 0
+    assert lib.lrei_create(8, None, B, ctypes.c_double(0.1), 0, 0, 64, None, ctypes.byref(h)) == -1  # r_max > 32
+    Bx = (ctypes.c_double * 3)(0.3, 0.0, 0.5)
+    assert lib.lrei_create(8, None, Bx, ctypes.c_double(0.1), 0, 0, 4, None, ctypes.byref(h)) == -2  # transverse field

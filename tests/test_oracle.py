@@ -345,3 +345,11 @@ def test_planted_dropped_term_in_qll_is_caught():
     f_wrong = 1j * de.comm(rho, H)          # damping term dropped
     C = de.comm(rho, H)
     assert not np.isclose(np.trace(H @ f_wrong).real, -kappa * np.linalg.norm(C) ** 2, rtol=1e-3)
+
+
+def test_hamiltonian_row_matches_dense():
+    n = 5
+    w = li.workload(2, n=n, r=2)
+    H = model.hamiltonian(n, w.bonds, w.B)
+    for b in (0, 7, 21, 31):
+        assert np.abs(model.hamiltonian_row(n, w.bonds, w.B, b) - H[b]).max() == 0
