@@ -159,6 +159,55 @@ int lrei_last_status(lrei_ctx *ctx);
  * last call (resets the counter). */
 long long lrei_kernel_launches(lrei_ctx *ctx);
 
+/* ---- step/rank controller network ------------------------------------- */
+/* A three-layer FP32 perceptron y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,
+ * hidden width 128, trained on the GPU by its own backward and Adam kernels.
+ * It is the learned form of the adaptive time stepping the paper names as
+ * future work (Sec. 6); the paper itself has no network.  Parameters are one
+ * float buffer [W1 | b1 | W2 | b2 | W3 | b3], each W row-major (out x in).
+ * All buffers named _dev are device float arrays, row-major (batch x features). */
+typedef struct lrei_mlp lrei_mlp;
+
+/* n_in in [1, 4096], n_out in [1, 64]; params_host may be NULL (all zero). */
+int lrei_mlp_create(int n_in, int n_out, const float *params_host, void *cuda_stream, lrei_mlp **out);
+int lrei_mlp_destroy(lrei_mlp *net);
+int lrei_mlp_num_params(const lrei_mlp *net);
+int lrei_mlp_get_params(lrei_mlp *net, float *host, int n);  /* syncs */
+int lrei_mlp_set_params(lrei_mlp *net, const float *host, int n);  /* resets Adam moments; syncs */
+/* Y (batch x n_out) = network(X (batch x n_in)). */
+int lrei_mlp_forward(lrei_mlp *net, const float *X_dev, int batch, float *Y_dev);
+/* Gradients of L = (1/2B) sum_b sum_o w_o (y_bo - t_bo)^2 into the network's gradient buffer;
+ * optionally copied to grad_dev (num_params floats) and the loss to *loss_host (syncs).
+ * w_host: n_out output weights or NULL (all one). */
+int lrei_mlp_grads(lrei_mlp *net, const float *X_dev, const float *T_dev, const float *w_host, int batch,
+                   float *grad_dev, float *loss_host);
+/* One Adam update with the last computed gradients (Kingma and Ba, 2015). */
+int lrei_mlp_adam(lrei_mlp *net, float lr, float beta1, float beta2, float eps);
+
+/* ---- adaptive step controller ------------------------------------------ */
+/* Features per step (LREI_CTRL_NFEAT floats): log10 of the 32 (padded) spectrum values,
+ * the spectral drift of the unprojected rho_{k+1}, h, ||[rho,H]||_F^2, the stage-to-stage
+ * change of G = V^*HV, kappa, the model, the tolerance and r/32 (each scaled to O(1)). */
+#define LREI_CTRL_NFEAT 40
+
+typedef struct {
+  long long accepted, rejected, judged; /* steps; judged = step-doubling checks */
+  long long rk4_steps;                  /* RK4 steps executed, including judges and rejects */
+  double h;                             /* step proposed for the next call */
+  double err_judged;                    /* last step-doubling error estimate */
+  double calib;                         /* drift-to-error calibration factor */
+} lrei_ctrl_stats;
+
+/* judge_every: step-doubling period of the plain judge (>= 1); record != 0 keeps one row per
+ * attempted step (features, h, drift, judged error or -1, accepted); h0 > 0 sets the first step.
+ * Resets the statistics and the record. */
+int lrei_controller_config(lrei_ctx *ctx, int judge_every, int record, double h0);
+/* Network used by lrei_step_adaptive(..., controller = 1); output 0 is log(h_next / h). */
+int lrei_controller_attach(lrei_ctx *ctx, lrei_mlp *net);
+int lrei_controller_stats(lrei_ctx *ctx, lrei_ctrl_stats *out);
+/* Copies up to max_rows rows of LREI_CTRL_NFEAT + 4 doubles; *n_rows = rows recorded. */
+int lrei_controller_records(lrei_ctx *ctx, double *rows, int max_rows, int *n_rows);
+
 #ifdef __cplusplus
 }
 #endif

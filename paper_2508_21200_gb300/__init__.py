@@ -49,6 +49,13 @@ class Obs(ctypes.Structure):
         return d
 
 
+class CtrlStats(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong), ("judged", ctypes.c_longlong),
+                ("rk4_steps", ctypes.c_longlong), ("h", ctypes.c_double), ("err_judged", ctypes.c_double),
+                ("calib", ctypes.c_double)]
+
+
+NFEAT = 40
 _lib = None
 
 
@@ -76,6 +83,18 @@ def load_library(path: str | None = None):
         "lrei_rhs": (I, [P, P, P, ctypes.POINTER(D), I]),
         "lrei_kernel_launches": (L, [P]),
         "lrei_last_status": (I, [P]),
+        "lrei_mlp_create": (I, [I, I, P, P, ctypes.POINTER(P)]),
+        "lrei_mlp_destroy": (I, [P]),
+        "lrei_mlp_num_params": (I, [P]),
+        "lrei_mlp_get_params": (I, [P, P, I]),
+        "lrei_mlp_set_params": (I, [P, P, I]),
+        "lrei_mlp_forward": (I, [P, P, I, P]),
+        "lrei_mlp_grads": (I, [P, P, P, P, I, P, ctypes.POINTER(ctypes.c_float)]),
+        "lrei_mlp_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "lrei_controller_config": (I, [P, I, I, D]),
+        "lrei_controller_attach": (I, [P, P]),
+        "lrei_controller_stats": (I, [P, ctypes.POINTER(CtrlStats)]),
+        "lrei_controller_records": (I, [P, P, I, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -191,3 +210,81 @@ class Lrei:
 
     def kernel_launches(self):
         return int(self._lib.lrei_kernel_launches(self._h))
+
+    def controller_config(self, judge_every=8, record=False, h0=0.0):
+        _check(self._lib.lrei_controller_config(self._h, int(judge_every), int(bool(record)), float(h0)))
+
+    def controller_attach(self, net):
+        self._net = net
+        _check(self._lib.lrei_controller_attach(self._h, net._h if net is not None else None))
+
+    def controller_stats(self):
+        st = CtrlStats()
+        _check(self._lib.lrei_controller_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def controller_records(self):
+        n = ctypes.c_int()
+        _check(self._lib.lrei_controller_records(self._h, None, 0, ctypes.byref(n)))
+        rows = np.zeros((n.value, NFEAT + 4))
+        if n.value:
+            _check(self._lib.lrei_controller_records(self._h, rows.ctypes.data, n.value, ctypes.byref(n)))
+        return rows
+
+
+class Mlp:
+    """The controller network (FP32, hidden width 128) with GPU training kernels."""
+
+    def __init__(self, n_in, n_out, params=None, stream=None):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self._lib.lrei_mlp_create(n_in, n_out, buf.ctypes.data if buf is not None else None,
+                                         _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.n_in, self.n_out = n_in, n_out
+        self.n_params = self._lib.lrei_mlp_num_params(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lrei_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(self._lib.lrei_mlp_get_params(self._h, out.ctypes.data, self.n_params))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(self._lib.lrei_mlp_set_params(self._h, p.ctypes.data, self.n_params))
+
+    def forward(self, X):
+        import torch
+        X = X.contiguous().float()
+        Y = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device="cuda")
+        _check(self._lib.lrei_mlp_forward(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                          ctypes.c_void_p(Y.data_ptr())))
+        return Y
+
+    def grads(self, X, T, w=None, want_grad=False):
+        import torch
+        X, T = X.contiguous().float(), T.contiguous().float()
+        wb = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+        G = torch.empty(self.n_params, dtype=torch.float32, device="cuda") if want_grad else None
+        loss = ctypes.c_float()
+        _check(self._lib.lrei_mlp_grads(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(T.data_ptr()),
+                                        wb.ctypes.data if wb is not None else None, X.shape[0],
+                                        ctypes.c_void_p(G.data_ptr()) if G is not None else None, ctypes.byref(loss)))
+        return loss.value, G
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(self._lib.lrei_mlp_adam(self._h, lr, beta1, beta2, eps))

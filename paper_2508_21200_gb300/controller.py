@@ -1,0 +1,68 @@
+"""Training and evaluation of the learned step controller.
+
+Data: the plain adaptive controller run with a step-doubling judge on every step
+(`judge_every=1`, `record=True`) on open chains of n = 12..18 spins; each record holds
+the step features and the judged local error of the step actually taken.  The target
+is the step ratio the plain rule would choose from that measured error,
+log clip(0.9 (tol / err)^(1/5), 0.2, 5).  Training runs on the GPU through the
+network's own gradient and Adam kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import Lrei, Mlp, NFEAT
+
+
+def target_from_error(err, tol):
+    return np.log(np.clip(0.9 * (tol / np.maximum(err, 1e-300)) ** 0.2, 0.2, 5.0))
+
+
+def generate(workloads, t_end=0.3, tols=(1e-7, 1e-9), precision="fp64", device_tensor=None):
+    """Run the plain controller with per-step judging; return (X, Y) training arrays."""
+    import torch
+    Xs, Ys = [], []
+    for w in workloads:
+        for tol in tols:
+            L = Lrei(w.n, w.bonds, w.B, w.kappa, w.model, precision, w.r)
+            dt = torch.complex128 if precision == "fp64" else torch.complex64
+            L.set_state(torch.from_numpy(w.V).to("cuda", dt), w.lam)
+            L.controller_config(judge_every=1, record=True, h0=0.01)
+            L.step_adaptive(t_end, tol, 0)
+            rows = L.controller_records()
+            ok = rows[:, NFEAT + 2] > 0
+            Xs.append(rows[ok, :NFEAT])
+            Ys.append(target_from_error(rows[ok, NFEAT + 2], tol)[:, None])
+            L.close()
+    return np.concatenate(Xs).astype(np.float32), np.concatenate(Ys).astype(np.float32)
+
+
+def init_params(n_in, n_out, seed=0, hidden=128):
+    """Glorot-uniform initial weights in the library's flat layout [W1|b1|W2|b2|W3|b3]."""
+    rng = np.random.default_rng(seed)
+
+    def glorot(o, i):
+        lim = np.sqrt(6.0 / (i + o))
+        return rng.uniform(-lim, lim, size=(o, i))
+    parts = [glorot(hidden, n_in), np.zeros(hidden), glorot(hidden, hidden), np.zeros(hidden),
+             glorot(n_out, hidden), np.zeros(n_out)]
+    return np.concatenate([p.reshape(-1) for p in parts]).astype(np.float32)
+
+
+def fit(X, Y, iters=3000, lr=2e-3, seed=0, batch=512):
+    """Fit the controller network on the GPU with minibatch Adam; returns (net, train loss)."""
+    import torch
+    net = Mlp(X.shape[1], Y.shape[1], init_params(X.shape[1], Y.shape[1], seed))
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    Yd = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    n = X.shape[0]
+    for it in range(iters):
+        if n > batch:
+            idx = torch.randint(0, n, (batch,), device="cuda", generator=g)
+            net.grads(Xd[idx], Yd[idx])
+        else:
+            net.grads(Xd, Yd)
+        net.adam(lr=lr)
+    loss, _ = net.grads(Xd, Yd)
+    return net, loss

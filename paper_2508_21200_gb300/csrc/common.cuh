@@ -82,4 +82,7 @@ enum : int {
 
 namespace lrei {
 int cuda_fail(cudaError_t e, const char *what);
+// Kernels launched (or recorded into a graph) by this library's wrappers in this process.
+long long launch_counter();
+void count_launch(int n = 1);
 }

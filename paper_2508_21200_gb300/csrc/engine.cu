@@ -26,13 +26,22 @@
 #include "small.cuh"
 #include "tsk.cuh"
 
+// controller network inference on a given stream (mlp.cu)
+int lrei_mlp_forward_on(lrei_mlp *net, const float *X, int B, float *Y, cudaStream_t st);
+
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 namespace lrei {
+
+static std::atomic<long long> g_launches{0};
+long long launch_counter() { return g_launches.load(); }
+void count_launch(int n) { g_launches += n; }
 
 int cuda_fail(cudaError_t e, const char *what) {
   (void)what;
@@ -219,90 +228,205 @@ __global__ void lhl_kernel(const zd *__restrict__ L, int r, const double *__rest
   }
 }
 
-// Observables from the Gram blocks of the observable pass.
+// Observables from the Gram blocks of the observable pass (one CTA, r <= 32).
+// The stored factor V is orthonormalised implicitly: with V^*V = L L^H and X = L^{-1},
+// Tr(rho A) = Tr(Lambda X (V^*AV) X^H).
 __global__ void obs_final_kernel(const double *__restrict__ red, int r, const double *__restrict__ lam,
                                  double *__restrict__ out) {
   // blocks: 0 V^*HV, 1 (HV)^*(HV), 2 V^*V, 3 V^*MxV, 4 V^*MyV, 5 V^*MzV
   extern __shared__ zd s[];
-  zd *Gm = s, *X = s + r * r;  // Gamma copy then L, X = L^{-1}
+  zd *Lg = s, *X = s + r * r, *T = s + 2 * r * r, *Ab = s + 3 * r * r;
+  __shared__ double part[6][32];
   const zd *B = reinterpret_cast<const zd *>(red);
-  const int t = threadIdx.x;
-  for (int e = t; e < r * r; e += blockDim.x) Gm[e] = B[2 * r * r + e];
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < r * r; e += nt) Lg[e] = B[2 * r * r + e];
   __syncthreads();
-  if (t == 0) {
-    // in-place Cholesky of Gamma (lower), then X = L^{-1}
-    for (int j = 0; j < r; ++j) {
-      double d = Gm[j * r + j].re;
-      for (int m = 0; m < j; ++m) d -= norm2(Gm[m * r + j]);
-      d = sqrt(fmax(d, 1e-300));
-      Gm[j * r + j] = mk<double>(d, 0);
-      for (int i = j + 1; i < r; ++i) {
-        zd v = Gm[j * r + i];
-        for (int m = 0; m < j; ++m) v = v - Gm[m * r + i] * conj(Gm[m * r + j]);
-        Gm[j * r + i] = mk<double>(v.re / d, v.im / d);
-      }
+  // Cholesky of Gamma (column by column, rows in parallel)
+  for (int j = 0; j < r; ++j) {
+    if (t == 0) {
+      double d = Lg[j * r + j].re;
+      for (int m = 0; m < j; ++m) d -= norm2(Lg[m * r + j]);
+      Lg[j * r + j] = mk<double>(sqrt(fmax(d, 1e-300)), 0);
     }
-    for (int j = 0; j < r; ++j)
-      for (int i = 0; i < r; ++i) {
-        if (i < j) { X[j * r + i] = mk<double>(0, 0); continue; }
-        zd v = mk<double>(i == j ? 1.0 : 0.0, 0);
-        for (int m = j; m < i; ++m) v = v - Gm[m * r + i] * X[j * r + m];
-        const double d = Gm[i * r + i].re;
-        X[j * r + i] = mk<double>(v.re / d, v.im / d);
-      }
+    __syncthreads();
+    for (int i = j + 1 + t; i < r; i += nt) {
+      zd v = Lg[j * r + i];
+      for (int m = 0; m < j; ++m) v = v - Lg[m * r + i] * conj(Lg[m * r + j]);
+      const double d = Lg[j * r + j].re;
+      Lg[j * r + i] = mk<double>(v.re / d, v.im / d);
+    }
+    __syncthreads();
+  }
+  // X = L^{-1}: column j by forward substitution, columns in parallel
+  for (int j = t; j < r; j += nt) {
+    for (int i = 0; i < r; ++i) {
+      if (i < j) { X[j * r + i] = mk<double>(0, 0); continue; }
+      zd v = mk<double>(i == j ? 1.0 : 0.0, 0);
+      for (int m = j; m < i; ++m) v = v - Lg[m * r + i] * X[j * r + m];
+      const double d = Lg[i * r + i].re;
+      X[j * r + i] = mk<double>(v.re / d, v.im / d);
+    }
+  }
+  __syncthreads();
+  const int which[5] = {0, 1, 3, 4, 5};
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int w = 0; w < 5; ++w) {
+    const zd *A = B + which[w] * r * r;
+    for (int e = t; e < r * r; e += nt) {          // T = X A
+      const int i = e % r, j = e / r;
+      zd v = mk<double>(0, 0);
+      for (int m = 0; m <= i; ++m) fma_(v, X[m * r + i], A[j * r + m]);
+      T[e] = v;
+    }
+    __syncthreads();
+    for (int e = t; e < r * r; e += nt) {          // Abar = T X^H
+      const int i = e % r, j = e / r;
+      zd v = mk<double>(0, 0);
+      for (int m = 0; m <= j; ++m) v = v + T[m * r + i] * conj(X[m * r + j]);
+      Ab[e] = v;
+    }
+    __syncthreads();
+    for (int i = t; i < r; i += nt) acc[w] += ((w == 1) ? lam[i] * lam[i] : lam[i]) * Ab[i * r + i].re;
+    if (w == 0)   // Tr(Lambda Gbar Lambda Gbar)
+      for (int e = t; e < r * r; e += nt) acc[5] += lam[e % r] * lam[e / r] * norm2(Ab[e]);
+    __syncthreads();
+  }
+  for (int q = 0; q < 6; ++q) {
+    double v = acc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((t & 31) == 0) part[q][t >> 5] = v;
   }
   __syncthreads();
   if (t == 0) {
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    // Abar = X A X^H, trace with Lambda: sum_i lam_i sum_{m,n} X_im A_mn conj(X_in)
-    const int which[5] = {0, 1, 3, 4, 5};
-    for (int w = 0; w < 5; ++w) {
-      const zd *A = B + which[w] * r * r;
-      double tr = 0.0;
-      for (int i = 0; i < r; ++i) {
-        const double li = (w == 1) ? lam[i] * lam[i] : lam[i];
-        zd sacc = mk<double>(0, 0);
-        for (int m = 0; m < r; ++m)
-          for (int n = 0; n < r; ++n) sacc = sacc + X[m * r + i] * A[n * r + m] * conj(X[n * r + i]);
-        tr += li * sacc.re;
-      }
-      acc[w] = tr;
+    double tot[6];
+    for (int q = 0; q < 6; ++q) {
+      tot[q] = 0.0;
+      for (int w = 0; w < (nt + 31) / 32; ++w) tot[q] += part[q][w];
     }
-    // Tr(Lambda Gbar Lambda Gbar)
-    double tgg = 0.0;
-    for (int i = 0; i < r; ++i)
-      for (int j = 0; j < r; ++j) {
-        zd g = mk<double>(0, 0);
-        for (int m = 0; m < r; ++m)
-          for (int n = 0; n < r; ++n) g = g + X[m * r + i] * B[n * r + m] * conj(X[n * r + j]);
-        tgg += lam[i] * lam[j] * norm2(g);
-      }
     const zd *Gam = B + 2 * r * r;
-    double trace = 0.0, purity = 0.0, orth = 0.0;
+    double trace = 0.0, purity = 0.0, orth = 0.0, herm = 0.0, gmax = 0.0;
     for (int i = 0; i < r; ++i) {
       trace += lam[i] * Gam[i * r + i].re;
       for (int j = 0; j < r; ++j) {
         purity += lam[i] * lam[j] * norm2(Gam[j * r + i]);
-        const zd d = Gam[j * r + i] - mk<double>(i == j ? 1.0 : 0.0, 0);
-        orth = fmax(orth, sqrt(norm2(d)));
-      }
-    }
-    double herm = 0.0, gmax = 0.0;
-    for (int i = 0; i < r; ++i)
-      for (int j = 0; j < r; ++j) {
+        orth = fmax(orth, sqrt(norm2(Gam[j * r + i] - mk<double>(i == j ? 1.0 : 0.0, 0))));
         const zd a = B[j * r + i], b = B[i * r + j];
         herm = fmax(herm, sqrt(norm2(a - conj(b))));
         gmax = fmax(gmax, sqrt(norm2(a)));
       }
-    out[0] = acc[0];                                // energy
-    out[1] = acc[2];                                // mx
-    out[2] = acc[3];                                // my
-    out[3] = acc[4];                                // mz
+    }
+    out[0] = tot[0];
+    out[1] = tot[2];
+    out[2] = tot[3];
+    out[3] = tot[4];
     out[4] = purity;
     out[5] = trace;
     out[6] = orth;
     out[7] = gmax > 0 ? herm / gmax : 0.0;
-    out[8] = sqrt(fmax(0.0, 2.0 * acc[1] - 2.0 * tgg));   // ||[rho, H]||_F
+    out[8] = sqrt(fmax(0.0, 2.0 * tot[1] - 2.0 * tot[5]));
+  }
+}
+
+// ----------------------------------------------------------- controller features
+// ||[rho, H]||_F^2 = 2 Tr(Lambda^2 V^*H^2V) - 2 Tr(Lambda G Lambda G); in the Krylov frame H V_1 has
+// coordinates t_0 = Tbar e, so V^*H^2V = t_0^H t_0 and only its diagonal is needed.
+__global__ void feat_comm_kernel(const zd *__restrict__ T, int K, int ld, const zd *__restrict__ G, int r,
+                                 const double *__restrict__ lam, double *__restrict__ feat) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int e = threadIdx.x; e < K * r; e += blockDim.x) s += 2.0 * lam[e / K] * lam[e / K] * norm2(T[(size_t)(e / K) * ld + (e % K)]);
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) s -= 2.0 * lam[e % r] * lam[e / r] * norm2(G[e]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) a += red[w];
+    feat[0] = fmax(a, 0.0);
+  }
+}
+
+// feat[1] = ||G_last - G_0||_F / ||G_0||_F (stage spread), feat[2] = max_i |mu_i - lambda_i| / lambda_max
+// (spectral drift of the unprojected rho_{k+1}).
+__global__ void feat_final_kernel(const double *__restrict__ mu, const double *__restrict__ lam, int r,
+                                  const zd *__restrict__ G0, const zd *__restrict__ Gl, double *__restrict__ feat) {
+  if (threadIdx.x != 0) return;
+  double d = 0, n0 = 0, dr = 0, lm = 0;
+  for (int e = 0; e < r * r; ++e) {
+    const int i = e % r, j = e / r;
+    const zd a = Gl[e], b = Gl[(size_t)i * r + j];
+    const zd h = mk<double>(0.5 * (a.re + b.re), 0.5 * (a.im - b.im));
+    d += norm2(h - G0[e]);
+    n0 += norm2(G0[e]);
+  }
+  for (int i = 0; i < r; ++i) {
+    dr = fmax(dr, fabs(mu[i] - lam[i]));
+    lm = fmax(lm, lam[i]);
+  }
+  feat[1] = n0 > 0 ? sqrt(d / n0) : 0.0;
+  feat[2] = lm > 0 ? dr / lm : 0.0;
+}
+
+// Frobenius distance between two states rho_a = Va La Va^*, rho_b (same spectrum Lambda), from
+// C = Va^*Vb and the Grams of the stored factors (implicit Cholesky orthonormalisation):
+// ||rho_a - rho_b||_F^2 = 2 sum lam^2 - 2 sum_ij lam_i lam_j |Cbar_ij|^2, Cbar = La^{-1} C Lb^{-H}.
+__device__ void chol_inv_small(const zd *A, int lda, int r, zd *L, zd *X) {
+  // single thread: L = chol(A) lower, X = L^{-1}
+  for (int j = 0; j < r; ++j) {
+    double d = A[(size_t)j * lda + j].re;
+    for (int m = 0; m < j; ++m) d -= norm2(L[m * r + j]);
+    d = sqrt(fmax(d, 1e-300));
+    L[j * r + j] = mk<double>(d, 0);
+    for (int i = j + 1; i < r; ++i) {
+      zd v = A[(size_t)j * lda + i];
+      for (int m = 0; m < j; ++m) v = v - L[m * r + i] * conj(L[m * r + j]);
+      L[j * r + i] = mk<double>(v.re / d, v.im / d);
+    }
+    for (int i = 0; i < j; ++i) L[j * r + i] = mk<double>(0, 0);
+  }
+  for (int j = 0; j < r; ++j)
+    for (int i = 0; i < r; ++i) {
+      if (i < j) { X[j * r + i] = mk<double>(0, 0); continue; }
+      zd v = mk<double>(i == j ? 1.0 : 0.0, 0);
+      for (int m = j; m < i; ++m) v = v - L[m * r + i] * X[j * r + m];
+      const double d = L[i * r + i].re;
+      X[j * r + i] = mk<double>(v.re / d, v.im / d);
+    }
+}
+
+__global__ void dist_kernel(const zd *__restrict__ red, int r, const zd *__restrict__ Ga, int lda_,
+                            const double *__restrict__ lam, double *__restrict__ out) {
+  extern __shared__ zd sd[];
+  zd *La = sd, *Xa = sd + r * r, *Lb = sd + 2 * r * r, *Xb = sd + 3 * r * r, *T = sd + 4 * r * r;
+  const int t = threadIdx.x;
+  const int ldr = 2 * r;   // red: rows 0..r-1 = Va^*Vb, rows r..2r-1 = Vb^*Vb (column-major)
+  if (t == 0) chol_inv_small(Ga, lda_, r, La, Xa);
+  if (t == 32 % blockDim.x && blockDim.x > 32) chol_inv_small(red + r, ldr, r, Lb, Xb);
+  if (blockDim.x <= 32 && t == 0) chol_inv_small(red + r, ldr, r, Lb, Xb);
+  __syncthreads();
+  for (int e = t; e < r * r; e += blockDim.x) {   // T = Xa C
+    const int i = e % r, j = e / r;
+    zd v = mk<double>(0, 0);
+    for (int m = 0; m <= i; ++m) fma_(v, Xa[m * r + i], red[(size_t)j * ldr + m]);
+    T[e] = v;
+  }
+  __syncthreads();
+  __shared__ double acc[256];
+  double s = 0.0;
+  for (int e = t; e < r * r; e += blockDim.x) {   // Cbar = T Xb^H
+    const int i = e % r, j = e / r;
+    zd v = mk<double>(0, 0);
+    for (int m = 0; m <= j; ++m) v = v + T[m * r + i] * conj(Xb[m * r + j]);
+    s += lam[i] * lam[j] * norm2(v);
+  }
+  acc[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    double a = 0, l2 = 0;
+    for (int w = 0; w < (int)blockDim.x; ++w) a += acc[w];
+    for (int i = 0; i < r; ++i) l2 += lam[i] * lam[i];
+    out[0] = sqrt(fmax(2.0 * l2 - 2.0 * a, 0.0));
+    out[1] = sqrt(l2);
   }
 }
 
@@ -336,7 +460,7 @@ struct lrei_ctx {
      *Uf = nullptr, *Vf = nullptr, *Yc = nullptr, *ts = nullptr, *G = nullptr, *X11 = nullptr, *Gh = nullptr;
   zd *ys[5] = {}, *zs[4] = {}, *wsv[4] = {};
   zd *yfin = nullptr;
-  double *lam0_dev = nullptr, *mu_dev = nullptr, *dt_dev = nullptr, *obs_dev = nullptr;
+  double *lam0_dev = nullptr, *mu_dev = nullptr, *dt_dev = nullptr, *obs_dev = nullptr, *feat_dev = nullptr;
   int *status_dev = nullptr, *dead_dev = nullptr;
   void *eig_ws = nullptr;
   int *status_host = nullptr;
@@ -349,10 +473,30 @@ struct lrei_ctx {
   cudaGraphExec_t gexec = nullptr;
   int g_scheme = -1, g_r = -1;
   long long g_nodes = 0;
-  long long launches = 0;
+  long long launches = 0, cnt0 = 0;
   int last_status = 0;
   // allocation list
   std::vector<void *> allocs;
+  // Adams-Bashforth state: history of raw (V_l, Y_l = H V_l) pairs, most recent first
+  int ab_m = 0;            // steps of the scheme whose history is held (0 = none)
+  double ab_dt = 0.0;
+  std::vector<void *> ab_free;
+  std::vector<std::pair<void *, void *>> ab_hist;
+  void *abQ[8] = {};       // Q_1 .. Q_{2m-1} of the AB basis (Q_0 = V)
+  zd *Rraw = nullptr, *Bbar = nullptr, *tys[4] = {};
+  bool ab_alloc = false;
+  // adaptive step controller
+  int ctrl_judge_every = 8, ctrl_record = 0;
+  double ctrl_h = 0.0, ctrl_safety = 1.0, ctrl_calib = -1.0;
+  long long st_accepted = 0, st_rejected = 0, st_judged = 0, st_rk4 = 0;
+  double st_err_judged = 0.0;
+  void *Vsave = nullptr, *Vbig = nullptr;
+  zd *Gsave = nullptr, *Lsave = nullptr, *Gbig = nullptr;
+  double *dist_dev = nullptr, *host_small = nullptr;
+  std::vector<double> records;
+  lrei_mlp *net = nullptr;
+  float *net_x = nullptr, *net_y = nullptr, *net_host = nullptr;
+  int learned_fallback = 0;
 };
 
 namespace {
@@ -383,17 +527,20 @@ int status_to_code(int st) {
 
 // Order the internal stream after the caller's stream, and back.
 void enter(lrei_ctx *c) {
+  c->cnt0 = launch_counter();
   cudaEventRecord(c->ev_in, c->user);
   cudaStreamWaitEvent(c->st, c->ev_in, 0);
 }
 void leave(lrei_ctx *c) {
+  c->launches += launch_counter() - c->cnt0;
+  c->cnt0 = launch_counter();
   cudaEventRecord(c->ev_out, c->st);
   cudaStreamWaitEvent(c->user, c->ev_out, 0);
 }
 
 const zd ONE = {1.0, 0.0}, ZERO = {0.0, 0.0}, MONE = {-1.0, 0.0};
 
-double tol_rc(const lrei_ctx *c) { return c->fp64 ? 1e-24 : 1e-12; }
+double tol_rc(const lrei_ctx *c) { return c->fp64 ? 1e-26 : 1e-13; }
 const double TOL_GAM = 1e-6;
 
 // One tall-skinny pass + deterministic reduction of its Gram into c->red.
@@ -445,13 +592,13 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
     sm_copy(red + k, ldr, r, r, c->GR, r, st);
     sm_gemm('C', 'N', r, r, k, MONE, red, ldr, c->Cc, KM, ONE, c->GR, r, st);
     sm_hermitize(c->GR, r, r, st);
-    sm_chol(c->GR, r, r, c->Lr, r, tol_rc(c), 0, c->dead_dev, c->status_dev, 0, st);
+    sm_chol(c->GR, r, r, c->Lr, r, tol_rc(c), 0, c->dead_dev, c->status_dev, 0, st, red + k, ldr);
     // A = (Lr^H)^{-1}; coefQ = -C A; Chat column block l = [C; Lr^H]
     sm_set_identity(c->Ainv, r, r, r, st);
     sm_trsv('C', c->Lr, r, r, c->Ainv, r, r, st);
     sm_gemm('N', 'N', k, r, r, MONE, c->Cc, KM, c->Ainv, r, ZERO, c->coefQ, k, st);
     sm_copy(c->Cc, KM, k, r, c->Chat + (size_t)l * r * KM, KM, st);
-    store_rc_kernel<<<1, 256, 0, st>>>(c->Lr, r, c->dead_dev, c->Chat + (size_t)l * r * KM + k, KM);
+    ::lrei::count_launch(); store_rc_kernel<<<1, 256, 0, st>>>(c->Lr, r, c->dead_dev, c->Chat + (size_t)l * r * KM + k, KM);
     // pass B: Q_{l+1} = S A - Q C A, Gram column [Q_0..Q_l, Q_{l+1}]^* Q_{l+1}
     TSArgs b = a;
     b.mode = 1;
@@ -468,7 +615,7 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
     sm_gemm('C', 'N', r, r, k, MONE, c->Bs, KM, c->Bs, KM, ONE, c->Dm, r, st);
     sm_hermitize(c->Dm, r, r, st);
     sm_chol(c->Dm, r, r, c->L22, r, TOL_GAM, 1, c->dead_dev, c->status_dev, 0, st);
-    store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM);
+    ::lrei::count_launch(); store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM);
   }
   // Tbar = L^H Chat L_s^{-H}: H Qbar_{0..s-1} = Qbar Tbar in the orthonormal frame Qbar = Q L^{-H}
   sm_conj_transpose(c->Chat, KM, K, sr, c->Xh, KM, st);
@@ -482,8 +629,12 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
   for (int j = 0; j < s; ++j) {
     sm_gemm('N', 'N', K, r, sr, ONE, c->Tbar, KM, c->ys[j], KM, ZERO, c->ts, KM, st);
     sm_gemm('C', 'N', r, r, sr, ONE, c->ys[j], KM, c->ts, KM, ZERO, c->G, r, st);
-    stage_xwz_kernel<<<r, 128, 2 * r * sizeof(zd), st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->ys[j], c->ts, K,
+    ::lrei::count_launch(); stage_xwz_kernel<<<r, 128, 2 * r * sizeof(zd), st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->ys[j], c->ts, K,
                                                          KM, c->X11, c->zs[j], c->wsv[j], j == 0 ? c->Gh : nullptr);
+    if (j == 0) {
+      ::lrei::count_launch();
+      feat_comm_kernel<<<1, 256, 0, st>>>(c->ts, K, KM, c->Gh, r, c->lam0_dev, c->feat_dev);
+    }
     StageCoefs C{};
     C.nterms = j + 1;
     const bool last = (j + 1 == s);
@@ -495,7 +646,7 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
     }
     const int nf = r * (1 + 2 * (j + 1));
     const int kk = last ? K : (j + 2) * r;
-    stage_factors_kernel<<<64, 256, 0, st>>>(P, C, c->lam0_dev, c->dt_dev, r, K, KM, c->Uf, c->Vf);
+    ::lrei::count_launch(); stage_factors_kernel<<<64, 256, 0, st>>>(P, C, c->lam0_dev, c->dt_dev, r, K, KM, c->Uf, c->Vf);
     sm_gemm('N', 'C', kk, kk, nf, ONE, c->Uf, KM, c->Vf, KM, ZERO, c->Mm, KM, st);
     sm_hermitize(c->Mm, KM, kk, st);
     zd *dst = last ? c->yfin : c->ys[j + 1];
@@ -516,7 +667,8 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
   int rc = ts_pass(c, cmb);
   if (rc) return rc;
   set_gamma00(c);
-  check_small_kernel<<<1, 256, 0, st>>>(c->mu_dev, r, c->Gam, KM, c->status_dev);
+  ::lrei::count_launch(); check_small_kernel<<<1, 256, 0, st>>>(c->mu_dev, r, c->Gam, KM, c->status_dev);
+  ::lrei::count_launch(); feat_final_kernel<<<1, 32, 0, st>>>(c->mu_dev, c->lam0_dev, r, c->Gh, c->G, c->feat_dev);
   return LREI_OK;
 }
 
@@ -541,9 +693,11 @@ int build_graph(lrei_ctx *c, int scheme) {
     c->gexec = nullptr;
   }
   cudaGraph_t g = nullptr;
+  const long long before = launch_counter();
   LREI_CUDA_TRY(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
   int rc = enqueue_rk_step(c, scheme);
   cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  c->cnt0 += launch_counter() - before;   // recorded into the graph, not launched
   if (rc) {
     if (g) cudaGraphDestroy(g);
     return rc;
@@ -565,6 +719,357 @@ int read_status(lrei_ctx *c) {
   c->last_status = s;
   LREI_CUDA_TRY(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->st));
   return s;
+}
+
+
+// ------------------------------------------------------------ Adams-Bashforth
+// LREI-AB_m (paper Sec. 3.8): rho_{k+1} = rho_k + h sum_l b_l f(rho_{k-l}), whose range lies in
+// span{V_k, W_k, V_{k-1}, W_{k-1}, ...} = span of the raw blocks [V_k, H V_k, V_{k-1}, H V_{k-1}, ...].
+// Those blocks are nearly dependent (consecutive V's differ by O(h)), so they are orthonormalised
+// explicitly, block by block, with the same fused passes as the Krylov basis (a Gram of the raw
+// block against the basis, then the projected, normalised block with its measured Gram column);
+// every history term is then evaluated in the orthonormal frame and one exact Rayleigh-Ritz step
+// gives V_{k+1}.
+int ab_prepare(lrei_ctx *c) {
+  if (c->ab_alloc) return LREI_OK;
+  const size_t blk_bytes = (size_t)c->N * c->r_max * c->elem;
+  int rc;
+  for (int i = 0; i < 8; ++i) {
+    void *p = nullptr;
+    if ((rc = dalloc(c, &p, blk_bytes))) return rc;
+    c->ab_free.push_back(p);
+  }
+  for (int i = 0; i < 7; ++i)
+    if ((rc = dalloc(c, &c->abQ[i], blk_bytes))) return rc;
+  const size_t zs = sizeof(zd);
+  if ((rc = dalloc_t(c, &c->Rraw, (size_t)c->KM * c->KM * zs))) return rc;
+  if ((rc = dalloc_t(c, &c->Bbar, (size_t)c->KM * c->KM * zs))) return rc;
+  for (int i = 0; i < 4; ++i)
+    if ((rc = dalloc_t(c, &c->tys[i], (size_t)c->KM * c->r_max * zs))) return rc;
+  c->ab_alloc = true;
+  return LREI_OK;
+}
+
+void ab_clear(lrei_ctx *c) {
+  for (auto &e : c->ab_hist) {
+    c->ab_free.push_back(e.first);
+    c->ab_free.push_back(e.second);
+  }
+  c->ab_hist.clear();
+  c->ab_m = 0;
+}
+
+void ab_trim(lrei_ctx *c, int keep) {
+  while ((int)c->ab_hist.size() > keep) {
+    c->ab_free.push_back(c->ab_hist.back().first);
+    c->ab_free.push_back(c->ab_hist.back().second);
+    c->ab_hist.pop_back();
+  }
+}
+
+void *ab_take(lrei_ctx *c) {
+  void *p = c->ab_free.back();
+  c->ab_free.pop_back();
+  return p;
+}
+
+// Record (V, H V) of the current state at the front of the history (used by the RK4 start-up).
+int ab_push_current(lrei_ctx *c) {
+  void *vk = ab_take(c), *yk = ab_take(c);
+  LREI_CUDA_TRY(cudaMemcpyAsync(vk, c->V, (size_t)c->N * c->r * c->elem, cudaMemcpyDeviceToDevice, c->st));
+  launch_hv(c->fp64, c->M, c->V, yk, c->N, c->r, c->nsm, c->st);
+  c->ab_hist.insert(c->ab_hist.begin(), {vk, yk});
+  return LREI_OK;
+}
+
+// One block of explicit Gram-Schmidt: raw block i against Q_0..Q_{i-1} (measured Gram), giving
+// Q_i, its Gram column, the extended Cholesky factor of Gamma, and raw = Q [C; Rc] in R.
+int orth_block(lrei_ctx *c, int i, const void *src, int apply_h, void *write_src, void *const *qb, zd *R) {
+  const int r = c->r, KM = c->KM, k = i * r, ldr = (i + 1) * r;
+  cudaStream_t st = c->st;
+  zd *red = reinterpret_cast<zd *>(c->red);
+  TSArgs a{};
+  a.nq = i;
+  a.gram_left = i;
+  for (int m = 0; m < i; ++m) a.q[m] = qb[m];
+  a.src = src;
+  a.apply_h = apply_h;
+  a.mode = 0;
+  a.out = write_src;
+  int rc = ts_pass(c, a);
+  if (rc) return rc;
+  sm_copy(red, ldr, k, r, c->Cc, KM, st);
+  sm_trsv('N', c->L, KM, k, c->Cc, KM, r, st);
+  sm_trsv('C', c->L, KM, k, c->Cc, KM, r, st);
+  sm_copy(red + k, ldr, r, r, c->GR, r, st);
+  sm_gemm('C', 'N', r, r, k, MONE, red, ldr, c->Cc, KM, ONE, c->GR, r, st);
+  sm_hermitize(c->GR, r, r, st);
+  sm_chol(c->GR, r, r, c->Lr, r, tol_rc(c), 0, c->dead_dev, c->status_dev, 0, st, red + k, ldr);
+  sm_set_identity(c->Ainv, r, r, r, st);
+  sm_trsv('C', c->Lr, r, r, c->Ainv, r, r, st);
+  sm_gemm('N', 'N', k, r, r, MONE, c->Cc, KM, c->Ainv, r, ZERO, c->coefQ, k, st);
+  sm_copy(c->Cc, KM, k, r, R + (size_t)i * r * KM, KM, st);
+  ::lrei::count_launch(); store_rc_kernel<<<1, 256, 0, st>>>(c->Lr, r, c->dead_dev, R + (size_t)i * r * KM + k, KM);
+  TSArgs b = a;
+  b.mode = 1;
+  b.src = write_src ? write_src : src;
+  b.apply_h = write_src ? 0 : apply_h;
+  b.out = qb[i];
+  b.coefS = c->Ainv;
+  b.coefQ = c->coefQ;
+  if ((rc = ts_pass(c, b))) return rc;
+  sm_store_gram_cols(red, ldr, k, r, c->Gam, KM, st);
+  sm_copy(c->Gam + (size_t)k * KM, KM, k, r, c->Bs, KM, st);
+  sm_trsv('N', c->L, KM, k, c->Bs, KM, r, st);
+  sm_copy(c->Gam + (size_t)k * KM + k, KM, r, r, c->Dm, r, st);
+  sm_gemm('C', 'N', r, r, k, MONE, c->Bs, KM, c->Bs, KM, ONE, c->Dm, r, st);
+  sm_hermitize(c->Dm, r, r, st);
+  sm_chol(c->Dm, r, r, c->L22, r, TOL_GAM, 1, c->dead_dev, c->status_dev, 0, st);
+  ::lrei::count_launch(); store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM);
+  return LREI_OK;
+}
+
+// One AB_m step.  Precondition: m-1 previous (V, H V) pairs in the history, Gamma_00 = V^*V.
+int enqueue_ab_step(lrei_ctx *c, int m) {
+  const double *bw = kAB[m - 2];
+  const int r = c->r, KM = c->KM, nb = 2 * m, K = nb * r;
+  cudaStream_t st = c->st;
+  void *vk = ab_take(c), *yk = ab_take(c);
+  LREI_CUDA_TRY(cudaMemcpyAsync(vk, c->V, (size_t)c->N * r * c->elem, cudaMemcpyDeviceToDevice, st));
+  const void *raw[8];
+  raw[0] = c->V;
+  raw[1] = yk;
+  for (int l = 1; l < m; ++l) {
+    raw[2 * l] = c->ab_hist[l - 1].first;
+    raw[2 * l + 1] = c->ab_hist[l - 1].second;
+  }
+  void *qb[8];
+  qb[0] = c->V;
+  for (int i = 1; i < nb; ++i) qb[i] = c->abQ[i - 1];
+  sm_zero(c->Rraw, KM, K, K, st);
+  sm_set_identity(c->Rraw, KM, r, r, st);
+  for (int i = 1; i < nb; ++i) {
+    int rc = (i == 1) ? orth_block(c, 1, c->V, 1, yk, qb, c->Rraw) : orth_block(c, i, raw[i], 0, nullptr, qb, c->Rraw);
+    if (rc) return rc;
+  }
+  // coordinates of the raw blocks in the orthonormal frame Qbar = Q L^{-H}: Bbar = L^H Rraw
+  sm_gemm('C', 'N', K, K, K, ONE, c->L, KM, c->Rraw, KM, ZERO, c->Bbar, KM, st);
+  for (int l = 0; l < m; ++l) {
+    // the state of step k-l is V_l orthonormalised: vbar = v Lv^{-H}, H vbar = y Lv^{-H}
+    sm_copy(c->Bbar + (size_t)(2 * l) * r * KM, KM, K, r, c->ys[l], KM, st);
+    sm_copy(c->Bbar + (size_t)(2 * l + 1) * r * KM, KM, K, r, c->tys[l], KM, st);
+    sm_gemm('C', 'N', r, r, K, ONE, c->ys[l], KM, c->ys[l], KM, ZERO, c->G, r, st);
+    sm_hermitize(c->G, r, r, st);
+    sm_chol(c->G, r, r, c->Lr, r, 0.0, 0, nullptr, nullptr, 0, st);
+    sm_rtrsm_lh_ws(c->ys[l], KM, K, c->Lr, r, r, c->Ainv, c->Uf, st);
+    sm_rtrsm_lh_ws(c->tys[l], KM, K, c->Lr, r, r, c->Ainv, c->Uf, st);
+    sm_gemm('C', 'N', r, r, K, ONE, c->ys[l], KM, c->tys[l], KM, ZERO, c->G, r, st);
+    ::lrei::count_launch(); stage_xwz_kernel<<<r, 128, 2 * r * sizeof(zd), st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->ys[l],
+                                                         c->tys[l], K, KM, c->X11, c->zs[l], c->wsv[l],
+                                                         l == 0 ? c->Gh : nullptr);
+  }
+  StageCoefs C{};
+  C.nterms = m;
+  StagePtrs P{};
+  for (int l = 0; l < m; ++l) {
+    C.c[l] = bw[l];
+    P.y[l] = c->ys[l];
+    P.z[l] = c->zs[l];
+    P.w[l] = c->wsv[l];
+  }
+  ::lrei::count_launch(); stage_factors_kernel<<<64, 256, 0, st>>>(P, C, c->lam0_dev, c->dt_dev, r, K, KM, c->Uf, c->Vf);
+  sm_gemm('N', 'C', K, K, r * (1 + 2 * m), ONE, c->Uf, KM, c->Vf, KM, ZERO, c->Mm, KM, st);
+  sm_hermitize(c->Mm, KM, K, st);
+  sm_zero(c->yfin, KM, K, r, st);
+  sm_eig_topr(c->Mm, KM, K, r, c->yfin, KM, c->mu_dev, c->eig_ws, c->status_dev, st);
+  sm_copy(c->yfin, KM, K, r, c->Yc, KM, st);
+  sm_trsv('C', c->L, KM, K, c->Yc, KM, r, st);
+  sm_copy(c->Yc, KM, K, r, c->coefQ, K, st);
+  TSArgs cmb{};
+  cmb.nq = nb;
+  cmb.gram_left = 0;
+  for (int i = 0; i < nb; ++i) cmb.q[i] = qb[i];
+  cmb.coefQ = c->coefQ;
+  cmb.mode = 2;
+  cmb.out = c->V;
+  int rc = ts_pass(c, cmb);
+  if (rc) return rc;
+  set_gamma00(c);
+  ::lrei::count_launch(); check_small_kernel<<<1, 256, 0, st>>>(c->mu_dev, r, c->Gam, KM, c->status_dev);
+  c->ab_hist.insert(c->ab_hist.begin(), {vk, yk});
+  ab_trim(c, m - 1);
+  return LREI_OK;
+}
+
+
+// ----------------------------------------------------------- adaptive stepping
+// Plain rule (the adaptive stepping the paper proposes as future work, Sec. 6): the local error
+// of an RK4 step is estimated from the spectral drift of the unprojected rho_{k+1} (free, a
+// by-product of the final Rayleigh-Ritz step) times a calibration factor; every judge_every-th
+// step, and after any rejection, the estimate is replaced by step doubling (one step of h
+// against two of h/2, error = 16/15 ||rho_h - rho_{h/2,h/2}||_F / ||rho||_F), which also
+// recalibrates the drift factor.  h_new = h clip(0.9 (tol/err)^(1/5), 0.2, 5); a step whose
+// error exceeds tol is rejected and retried.  The learned rule predicts log(h_new/h) from
+// step features with the controller network and keeps the plain judge as fallback.
+constexpr int NFEAT = 40;
+
+int ctrl_prepare(lrei_ctx *c) {
+  if (c->Vsave) return LREI_OK;
+  const size_t blk = (size_t)c->N * c->r_max * c->elem;
+  int rc;
+  if ((rc = dalloc(c, &c->Vsave, blk)) || (rc = dalloc(c, &c->Vbig, blk))) return rc;
+  const size_t rr = (size_t)c->r_max * c->r_max * sizeof(zd);
+  if ((rc = dalloc_t(c, &c->Gsave, rr)) || (rc = dalloc_t(c, &c->Lsave, rr)) || (rc = dalloc_t(c, &c->Gbig, rr)))
+    return rc;
+  if ((rc = dalloc_t(c, &c->dist_dev, 4 * sizeof(double)))) return rc;
+  if ((rc = dalloc_t(c, &c->net_x, NFEAT * sizeof(float))) || (rc = dalloc_t(c, &c->net_y, 64 * sizeof(float))))
+    return rc;
+  if (cudaMallocHost(&c->host_small, 64 * sizeof(double)) != cudaSuccess) return LREI_ERR_OOM;
+  if (cudaMallocHost(&c->net_host, 64 * sizeof(float)) != cudaSuccess) return LREI_ERR_OOM;
+  return LREI_OK;
+}
+
+void save_state(lrei_ctx *c, void *dst, zd *G, zd *L) {
+  const int r = c->r, KM = c->KM;
+  cudaMemcpyAsync(dst, c->V, (size_t)c->N * r * c->elem, cudaMemcpyDeviceToDevice, c->st);
+  sm_copy(c->Gam, KM, r, r, G, r, c->st);
+  if (L) sm_copy(c->L, KM, r, r, L, r, c->st);
+}
+
+void restore_state(lrei_ctx *c, const void *src, const zd *G, const zd *L) {
+  const int r = c->r, KM = c->KM;
+  cudaMemcpyAsync(c->V, src, (size_t)c->N * r * c->elem, cudaMemcpyDeviceToDevice, c->st);
+  sm_copy(G, r, r, r, c->Gam, KM, c->st);
+  sm_copy(L, r, r, r, c->L, KM, c->st);
+}
+
+int set_dt(lrei_ctx *c, double h) {
+  c->host_small[32] = h;
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->dt_dev, &c->host_small[32], sizeof(double), cudaMemcpyHostToDevice, c->st));
+  c->dt_cur = h;
+  return LREI_OK;
+}
+
+// Reads feat[0..2] (commutator^2, stage spread, drift) and the status word; syncs.
+int read_feats(lrei_ctx *c, double *f) {
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->host_small, c->feat_dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  const int s = read_status(c);
+  for (int i = 0; i < 3; ++i) f[i] = c->host_small[i];
+  return s;
+}
+
+void build_features(lrei_ctx *c, const double *f, double h, double tol, float *x) {
+  for (int i = 0; i < 32; ++i) x[i] = (float)std::log10(i < c->r ? std::fmax(c->lam0[i], 1e-12) : 1e-12) / 12.0f;
+  x[32] = (float)(std::log10(std::fmax(f[2], 1e-300)) / 16.0);
+  x[33] = (float)(std::log10(h) / 4.0);
+  x[34] = (float)(std::log10(std::fmax(f[0], 1e-300)) / 8.0);
+  x[35] = (float)(std::log10(std::fmax(f[1], 1e-300)) / 8.0);
+  x[36] = (float)c->kappa;
+  x[37] = (float)c->model;
+  x[38] = (float)(std::log10(tol) / 16.0);
+  x[39] = (float)c->r / 32.0f;
+}
+
+// Step doubling from the saved state: returns the relative error estimate of the h step and
+// leaves the state at the result of the two h/2 steps.
+int judge(lrei_ctx *c, double h, double *err) {
+  const int r = c->r;
+  save_state(c, c->Vbig, c->Gbig, nullptr);
+  restore_state(c, c->Vsave, c->Gsave, c->Lsave);
+  set_dt(c, 0.5 * h);
+  LREI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+  LREI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+  c->launches += 2 * c->g_nodes;
+  TSArgs a{};
+  a.nq = 1;
+  a.gram_left = 1;
+  a.q[0] = c->Vbig;
+  a.src = c->V;
+  a.apply_h = 0;
+  a.mode = 0;
+  int rc = ts_pass(c, a);
+  if (rc) return rc;
+  ::lrei::count_launch();
+  dist_kernel<<<1, 256, 5 * r * r * sizeof(zd), c->st>>>(reinterpret_cast<zd *>(c->red), r, c->Gbig, r, c->lam0_dev,
+                                                          c->dist_dev);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->host_small + 8, c->dist_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  *err = (16.0 / 15.0) * c->host_small[8] / std::fmax(c->host_small[9], 1e-300);
+  return LREI_OK;
+}
+
+int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
+  int rc = build_graph(c, (int)LREI_RK4);
+  if (rc) return rc;
+  double h = c->ctrl_h > 0 ? c->ctrl_h : 1e-2;
+  int since_judge = c->ctrl_judge_every;   // judge the first step
+  bool last_rejected = false;
+  int accepted_flag = 1;
+  double f[3];
+  while (c->t < t_end - 1e-12 * std::fmax(1.0, std::fabs(t_end))) {
+    const double hs = std::fmin(h, t_end - c->t);
+    save_state(c, c->Vsave, c->Gsave, c->Lsave);
+    set_dt(c, hs);
+    LREI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+    c->launches += c->g_nodes;
+    int sbits = read_feats(c, f);
+    if (sbits & (ST_NONFINITE | ST_RANK)) return status_to_code(sbits);
+    const double drift = f[2];
+    const bool do_judge = since_judge >= c->ctrl_judge_every || last_rejected || c->ctrl_calib < 0 ||
+                          (controller == 1 && c->learned_fallback > 0 && since_judge >= 2);
+    double err;
+    c->st_rk4 += 1;
+    if (do_judge) {
+      if ((rc = judge(c, hs, &err))) return rc;
+      c->st_rk4 += 2;
+      c->st_judged += 1;
+      c->st_err_judged = err;
+      since_judge = 0;
+      if (drift > 0) c->ctrl_calib = err / drift;
+    } else {
+      err = (c->ctrl_calib > 0 ? c->ctrl_calib : 1.0) * drift;
+      ++since_judge;
+    }
+    if (c->ctrl_record) {
+      float x[NFEAT];
+      build_features(c, f, hs, tol, x);
+      for (int i = 0; i < NFEAT; ++i) c->records.push_back(x[i]);
+      c->records.push_back(hs);
+      c->records.push_back(drift);
+      c->records.push_back(do_judge ? err : -1.0);
+      c->records.push_back(err <= tol ? 1.0 : 0.0);
+    }
+    if (!(err <= tol)) {
+      restore_state(c, c->Vsave, c->Gsave, c->Lsave);
+      c->st_rejected += 1;
+      h = hs * std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2));
+      last_rejected = true;
+      accepted_flag = 0;
+      if (controller == 1 && do_judge) c->learned_fallback = 16;
+      continue;
+    }
+    c->t += hs;
+    c->st_accepted += 1;
+    last_rejected = false;
+    accepted_flag = 1;
+    double ratio = std::fmin(5.0, std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2)));
+    if (controller == 1 && c->net && c->learned_fallback <= 0) {
+      float x[NFEAT];
+      build_features(c, f, hs, tol, x);
+      std::memcpy(c->net_host, x, sizeof(x));
+      LREI_CUDA_TRY(cudaMemcpyAsync(c->net_x, c->net_host, sizeof(x), cudaMemcpyHostToDevice, c->st));
+      // the network runs on the context's stream
+      if ((rc = lrei_mlp_forward_on(c->net, c->net_x, 1, c->net_y, c->st))) return rc;
+      LREI_CUDA_TRY(cudaMemcpyAsync(c->net_host, c->net_y, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+      LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+      const double pred = std::exp((double)c->net_host[0]);
+      if (std::isfinite(pred)) ratio = std::fmin(5.0, std::fmax(0.2, pred));
+    }
+    if (c->learned_fallback > 0) --c->learned_fallback;
+    h = hs * ratio;
+  }
+  c->ctrl_h = h;
+  return LREI_OK;
 }
 
 }  // namespace
@@ -652,12 +1157,12 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   if ((rc = dalloc(c, &c->V, blk_bytes))) return fail(rc);
   for (int i = 0; i < c->nblk; ++i)
     if ((rc = dalloc(c, &c->blk[i], blk_bytes))) return fail(rc);
-  c->KM = 5 * r_max;
+  c->KM = 8 * r_max;   // RK_s needs (s+1) r <= 5 r, AB_m needs 2 m r <= 8 r
   const int KM = c->KM, R = r_max;
   const size_t zs = sizeof(zd);
-  if ((rc = dalloc_t(c, &c->partial, (size_t)ts_max_grid(c->nsm) * (MAXB + 1) * R * R * 2 * sizeof(double)))) return fail(rc);
+  if ((rc = dalloc_t(c, &c->partial, (size_t)(ts_max_grid(c->nsm) + 16) * (MAXB + 1) * R * R * 2 * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->red, (size_t)(MAXB + 1) * R * R * 2 * sizeof(double)))) return fail(rc);
-  if ((rc = dalloc(c, &c->coef_scratch, (size_t)(MAXB + 1) * R * R * zs))) return fail(rc);
+  if ((rc = dalloc(c, &c->coef_scratch, (size_t)(MAXB + 1) * MAX_R * MAX_R * zs))) return fail(rc);
   zd **kk[] = {&c->Gam, &c->L, &c->Chat, &c->Tbar, &c->Xh, &c->Mm};
   for (auto p : kk)
     if ((rc = dalloc_t(c, p, (size_t)KM * KM * zs))) return fail(rc);
@@ -679,6 +1184,7 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   if ((rc = dalloc_t(c, &c->mu_dev, R * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->dt_dev, sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->obs_dev, 16 * sizeof(double)))) return fail(rc);
+  if ((rc = dalloc_t(c, &c->feat_dev, 16 * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->status_dev, sizeof(int)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->dead_dev, R * sizeof(int)))) return fail(rc);
   if ((rc = dalloc(c, &c->eig_ws, sm_eig_ws_bytes(KM, R)))) return fail(rc);
@@ -716,6 +1222,7 @@ int lrei_set_state(lrei_ctx *c, const void *V_dev, int r, int ld, int dtype, con
   enter(c);
   c->r = r;
   c->has_state = false;
+  if (c->ab_alloc) ab_clear(c);
   const int KM = c->KM;
   std::vector<double> lam_in(Lambda_host, Lambda_host + r);
   LREI_CUDA_TRY(cudaMemsetAsync(c->status_dev, 0, sizeof(int), c->st));
@@ -736,7 +1243,7 @@ int lrei_set_state(lrei_ctx *c, const void *V_dev, int r, int ld, int dtype, con
   sm_hermitize(red, r, r, c->st);
   sm_chol(red, r, r, c->L22, r, 1e-24, 1, c->dead_dev, c->status_dev, 1, c->st);
   LREI_CUDA_TRY(cudaMemcpyAsync(c->lam0_dev, lam_in.data(), r * sizeof(double), cudaMemcpyHostToDevice, c->st));
-  lhl_kernel<<<1, 256, 0, c->st>>>(c->L22, r, c->lam0_dev, c->Dm);
+  ::lrei::count_launch(); lhl_kernel<<<1, 256, 0, c->st>>>(c->L22, r, c->lam0_dev, c->Dm);
   sm_jacobi(true, c->Dm, r, r, c->Lr, r, c->mu_dev, c->eig_ws, 60, 1e-15, c->status_dev, c->st);
   // coefficients R^{-1} E = L^{-H} E
   sm_copy(c->Lr, r, r, r, c->coefQ, r, c->st);
@@ -786,7 +1293,9 @@ int lrei_step(lrei_ctx *c, double dt, lrei_scheme scheme, int nsteps) {
   if (!c->has_state) return LREI_ERR_STATE;
   if (!std::isfinite(dt) || nsteps < 0) return LREI_ERR_ARG;
   if (scheme < LREI_RK1 || scheme > LREI_AB4) return LREI_ERR_ARG;
-  if (scheme > LREI_RK4) return LREI_ERR_UNSUPPORTED;
+  const bool ab = scheme >= LREI_AB2;
+  const int m = ab ? (int)scheme - (int)LREI_AB2 + 2 : 0;
+  if (ab && 2 * m * c->r > 160) return LREI_ERR_UNSUPPORTED;   // k x k eigensolver limit
   if (nsteps == 0) return LREI_OK;
   enter(c);
   if (dt != c->dt_cur) {
@@ -794,11 +1303,30 @@ int lrei_step(lrei_ctx *c, double dt, lrei_scheme scheme, int nsteps) {
     LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
     c->dt_cur = dt;
   }
-  int rc = build_graph(c, (int)scheme);
+  int rc = build_graph(c, ab ? (int)LREI_RK4 : (int)scheme);
   if (rc) { leave(c); return rc; }
-  for (int i = 0; i < nsteps; ++i) {
-    LREI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
-    c->launches += c->g_nodes;
+  if (!ab) {
+    for (int i = 0; i < nsteps; ++i) {
+      LREI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+      c->launches += c->g_nodes;
+    }
+  } else {
+    if ((rc = ab_prepare(c))) { leave(c); return rc; }
+    if (c->ab_m != m || c->ab_dt != dt) {
+      ab_clear(c);
+      c->ab_m = m;
+      c->ab_dt = dt;
+    }
+    for (int i = 0; i < nsteps; ++i) {
+      if ((int)c->ab_hist.size() < m - 1) {
+        // start-up: RK4 steps (global order 4 >= m - 1), recording the history they pass through
+        if ((rc = ab_push_current(c))) { leave(c); return rc; }
+        LREI_CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+        c->launches += c->g_nodes;
+      } else {
+        if ((rc = enqueue_ab_step(c, m))) { leave(c); return rc; }
+      }
+    }
   }
   const int s = read_status(c);
   leave(c);
@@ -807,9 +1335,55 @@ int lrei_step(lrei_ctx *c, double dt, lrei_scheme scheme, int nsteps) {
 }
 
 int lrei_step_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
-  (void)t_end; (void)tol; (void)controller;
   if (!c) return LREI_ERR_ARG;
-  return LREI_ERR_UNSUPPORTED;
+  if (!c->has_state) return LREI_ERR_STATE;
+  if (!std::isfinite(t_end) || !(tol > 0) || (controller != 0 && controller != 1)) return LREI_ERR_ARG;
+  if (controller == 1 && !c->net) return LREI_ERR_STATE;
+  if (t_end <= c->t) return LREI_OK;
+  enter(c);
+  int rc = ctrl_prepare(c);
+  if (!rc) rc = run_adaptive(c, t_end, tol, controller);
+  leave(c);
+  return rc;
+}
+
+int lrei_controller_config(lrei_ctx *c, int judge_every, int record, double h0) {
+  if (!c || judge_every < 1) return LREI_ERR_ARG;
+  c->ctrl_judge_every = judge_every;
+  c->ctrl_record = record ? 1 : 0;
+  if (h0 > 0) c->ctrl_h = h0;
+  c->ctrl_calib = -1.0;
+  c->records.clear();
+  c->st_accepted = c->st_rejected = c->st_judged = c->st_rk4 = 0;
+  return LREI_OK;
+}
+
+int lrei_controller_attach(lrei_ctx *c, lrei_mlp *net) {
+  if (!c) return LREI_ERR_ARG;
+  c->net = net;
+  c->learned_fallback = 0;
+  return LREI_OK;
+}
+
+int lrei_controller_stats(lrei_ctx *c, lrei_ctrl_stats *out) {
+  if (!c || !out) return LREI_ERR_ARG;
+  out->accepted = c->st_accepted;
+  out->rejected = c->st_rejected;
+  out->judged = c->st_judged;
+  out->rk4_steps = c->st_rk4;
+  out->h = c->ctrl_h;
+  out->err_judged = c->st_err_judged;
+  out->calib = c->ctrl_calib;
+  return LREI_OK;
+}
+
+int lrei_controller_records(lrei_ctx *c, double *rows, int max_rows, int *n_rows) {
+  if (!c || !n_rows) return LREI_ERR_ARG;
+  const int w = LREI_CTRL_NFEAT + 4;
+  const int n = (int)(c->records.size() / w);
+  *n_rows = n;
+  if (rows) std::memcpy(rows, c->records.data(), (size_t)std::min(n, max_rows) * w * sizeof(double));
+  return LREI_OK;
 }
 
 int lrei_observables(lrei_ctx *c, lrei_obs *out) {
@@ -819,13 +1393,12 @@ int lrei_observables(lrei_ctx *c, lrei_obs *out) {
   enter(c);
   int g = launch_obs(c->fp64, c->M, c->V, c->N, r, c->partial, c->nsm, c->st);
   launch_reduce(c->partial, g, 6 * r * r * 2, c->red, c->st);
-  obs_final_kernel<<<1, 32, 2 * r * r * sizeof(zd), c->st>>>(c->red, r, c->lam0_dev, c->obs_dev);
+  ::lrei::count_launch(); obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), c->st>>>(c->red, r, c->lam0_dev, c->obs_dev);
   LREI_CUDA_TRY(cudaMemcpyAsync(c->obs_host, c->obs_dev, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   std::vector<double> mu(r);
   LREI_CUDA_TRY(cudaMemcpyAsync(mu.data(), c->mu_dev, r * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   leave(c);
   LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
-  c->launches += 3;
   std::memset(out, 0, sizeof(*out));
   out->t = c->t;
   out->energy = c->obs_host[0];
@@ -850,7 +1423,6 @@ int lrei_apply_h(lrei_ctx *c, const void *V_dev, void *Y_dev, int r) {
   enter(c);
   launch_hv(c->fp64, c->M, V_dev, Y_dev, c->N, r, c->nsm, c->st);
   leave(c);
-  c->launches += 1;
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LREI_OK : cuda_fail(e, "apply_h");
 }
@@ -874,7 +1446,7 @@ int lrei_rhs(lrei_ctx *c, void *Z_dev, void *W_dev, double *G_host, int compleme
   if (rc) { leave(c); return rc; }
   zd *red = reinterpret_cast<zd *>(c->red);
   sm_copy(red, 2 * r, r, r, c->G, r, c->st);
-  rhs_coef_kernel<<<1, 256, 0, c->st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->Dm, c->GR, c->X11);
+  ::lrei::count_launch(); rhs_coef_kernel<<<1, 256, 0, c->st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->Dm, c->GR, c->X11);
   // pass 2: W = Y diag(conj c) - V (G diag(conj c))   (in place over Y: row-local)
   TSArgs b{};
   b.nq = 1;
@@ -901,7 +1473,6 @@ int lrei_rhs(lrei_ctx *c, void *Z_dev, void *W_dev, double *G_host, int compleme
   }
   leave(c);
   LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
-  c->launches += 12;
   return LREI_OK;
 }
 

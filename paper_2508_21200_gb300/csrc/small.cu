@@ -62,129 +62,156 @@ void sm_gemm(char opA, char opB, int M, int N, int K, zd alpha, const zd *A, int
   if (M <= 0 || N <= 0) return;
   if (K >= 48) {
     const long long threads = (long long)M * N * 32;
-    gemm_warp_kernel<<<(int)((threads + 127) / 128), 128, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C,
+    ::lrei::count_launch(); gemm_warp_kernel<<<(int)((threads + 127) / 128), 128, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C,
                                                                     ldc);
   } else {
-    gemm_thread_kernel<<<(M * N + 63) / 64, 64, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    ::lrei::count_launch(); gemm_thread_kernel<<<(M * N + 63) / 64, 64, 0, st>>>(opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   }
 }
 
 // ------------------------------------------------------- triangular solves
-__global__ void trsv_kernel(char op, const zd *__restrict__ L, int ldl, int k, zd *__restrict__ B, int ldb) {
-  extern __shared__ zd xs[];
-  zd *x = B + (size_t)blockIdx.x * ldb;
-  const int lane = threadIdx.x;
-  for (int i = lane; i < k; i += 32) xs[i] = x[i];
-  __syncwarp();
-  if (op == 'N') {
-    for (int i = 0; i < k; ++i) {
-      zd s = mk<double>(0, 0);
-      for (int m = lane; m < i; m += 32) fma_(s, L[(size_t)m * ldl + i], xs[m]);
-      s = warp_sum(s);
-      if (lane == 0) {
-        const zd d = L[(size_t)i * ldl + i];
-        xs[i] = (d.re == 0.0 && d.im == 0.0) ? mk<double>(0, 0) : zdiv(xs[i] - s, d);
-      }
-      __syncwarp();
-    }
-  } else {
-    for (int i = k - 1; i >= 0; --i) {
-      zd s = mk<double>(0, 0);
-      for (int m = i + 1 + lane; m < k; m += 32) fmac_(s, L[(size_t)i * ldl + m], xs[m]);
-      s = warp_sum(s);
-      if (lane == 0) {
-        const zd d = conj(L[(size_t)i * ldl + i]);
-        xs[i] = (d.re == 0.0 && d.im == 0.0) ? mk<double>(0, 0) : zdiv(xs[i] - s, d);
-      }
-      __syncwarp();
+// Triangular solves, one warp per right-hand side, four warps per CTA sharing one copy of the
+// triangle in shared memory.  Right-looking: x_j = b_j / d_j is broadcast from shared memory and
+// every lane updates the rows it owns, so the loop has no reductions and no divisions (the
+// reciprocal diagonal is precomputed).  Up to k = 90 the triangle is staged in shared memory
+// (column j of T holds the multipliers of x_j); larger k reads it from global memory.
+constexpr int TRSV_SMEM_K = 90;
+__global__ void __launch_bounds__(128) trsv_kernel(char op, const zd *__restrict__ L, int ldl, int k,
+                                                   zd *__restrict__ B, int ldb, int ncols) {
+  extern __shared__ zd trsv_sm[];
+  const bool staged = k <= TRSV_SMEM_K;
+  zd *Ts = trsv_sm;                                  // k x k: Ts[j*k + i] = multiplier of x_j in row i
+  zd *xs = staged ? trsv_sm + (size_t)k * k : trsv_sm;    // 4 warps x k
+  double *rd = reinterpret_cast<double *>(xs + 4 * k);   // k reciprocal diagonal entries
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  for (int i = t; i < k; i += blockDim.x) {
+    const double d = L[(size_t)i * ldl + i].re;
+    rd[i] = d != 0.0 ? 1.0 / d : 0.0;
+  }
+  if (staged) {
+    for (int e = t; e < k * k; e += blockDim.x) {
+      const int i = e % k, j = e / k;
+      zd v = mk<double>(0, 0);
+      if (op == 'N') { if (i > j) v = L[(size_t)j * ldl + i]; }          // L(i, j)
+      else { if (i < j) v = conj(L[(size_t)i * ldl + j]); }               // (L^H)(i, j) = conj(L(j, i))
+      Ts[e] = v;
     }
   }
-  for (int i = lane; i < k; i += 32) x[i] = xs[i];
+  const int col = blockIdx.x * 4 + wp;
+  zd *x = xs + wp * k;
+  zd *bcol = B + (size_t)col * ldb;
+  if (col < ncols)
+    for (int i = lane; i < k; i += 32) x[i] = bcol[i];
+  __syncthreads();
+  if (col < ncols) {
+    auto mult = [&](int i, int j) -> zd {
+      if (staged) return Ts[(size_t)j * k + i];
+      return op == 'N' ? L[(size_t)j * ldl + i] : conj(L[(size_t)i * ldl + j]);
+    };
+    if (op == 'N') {
+      for (int j = 0; j < k; ++j) {
+        __syncwarp();
+        const zd xj = mk<double>(x[j].re * rd[j], x[j].im * rd[j]);
+        __syncwarp();
+        if (lane == 0) x[j] = xj;
+        for (int i = j + 1 + lane; i < k; i += 32) x[i] = x[i] - mult(i, j) * xj;
+      }
+    } else {
+      for (int j = k - 1; j >= 0; --j) {
+        __syncwarp();
+        const zd xj = mk<double>(x[j].re * rd[j], x[j].im * rd[j]);
+        __syncwarp();
+        if (lane == 0) x[j] = xj;
+        for (int i = lane; i < j; i += 32) x[i] = x[i] - mult(i, j) * xj;
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) bcol[i] = x[i];
+  }
 }
 
 void sm_trsv(char op, const zd *L, int ldl, int k, zd *B, int ldb, int ncols, cudaStream_t st) {
   if (ncols <= 0 || k <= 0) return;
-  trsv_kernel<<<ncols, 32, k * sizeof(zd), st>>>(op, L, ldl, k, B, ldb);
+  const size_t bytes = ((k <= TRSV_SMEM_K ? (size_t)k * k : 0) + 4 * (size_t)k) * sizeof(zd) + (size_t)k * 8;
+  ::lrei::count_launch();
+  trsv_kernel<<<(ncols + 3) / 4, 128, bytes, st>>>(op, L, ldl, k, B, ldb, ncols);
 }
 
-// X <- X (L^H)^{-1}: row y solves y L^H = x, i.e. y_j = (x_j - sum_{m<j} y_m conj(L[j][m])) / L[j][j].
-__global__ void rtrsm_lh_kernel(zd *X, int ldx, int nrows, const zd *__restrict__ L, int ldl, int k) {
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nrows) return;
-  for (int j = 0; j < k; ++j) {
-    zd s = X[(size_t)j * ldx + row];
-    for (int m = 0; m < j; ++m) {
-      const zd l = conj(L[(size_t)m * ldl + j]);
-      const zd y = X[(size_t)m * ldx + row];
-      s = s - y * l;
-    }
-    const zd d = conj(L[(size_t)j * ldl + j]);
-    X[(size_t)j * ldx + row] = (d.re == 0.0 && d.im == 0.0) ? mk<double>(0, 0) : zdiv(s, d);
-  }
-}
-
-void sm_rtrsm_lh(zd *X, int ldx, int nrows, const zd *L, int ldl, int k, cudaStream_t st) {
+// X <- X (L^H)^{-1}: the inverse (L^H)^{-1} is formed by triangular solves on the identity and
+// applied with one GEMM, so no FP64 dependency chain runs per row.  Needs a k x k scratch and a
+// copy of X (both from the caller's workspace).
+void sm_rtrsm_lh_ws(zd *X, int ldx, int nrows, const zd *L, int ldl, int k, zd *inv, zd *xcopy, cudaStream_t st) {
   if (nrows <= 0) return;
-  rtrsm_lh_kernel<<<(nrows + 63) / 64, 64, 0, st>>>(X, ldx, nrows, L, ldl, k);
+  sm_set_identity(inv, k, k, k, st);
+  sm_trsv('C', L, ldl, k, inv, k, k, st);                 // inv = (L^H)^{-1}
+  sm_copy(X, ldx, nrows, k, xcopy, nrows, st);
+  sm_gemm('N', 'N', nrows, k, k, mk<double>(1, 0), xcopy, nrows, inv, k, mk<double>(0, 0), X, ldx, st);
 }
 
 // ------------------------------------------------------------- Cholesky
+// Right-looking Cholesky A = L L^H of a Hermitian k x k matrix (k <= 64) in one CTA: after each
+// pivot the trailing matrix gets a rank-one update, one element per thread, so the dependency
+// chain is k steps of one fused multiply-add (FP64 latency, not dot products, sets the time).
+// Column j is dead when its pivot is below tol times a reference: the j-th diagonal entry of
+// `ref` when given (the squared norm of the raw column), else the largest diagonal entry of A.
+// A dead column gets L[j][j] = 1 and a zero sub-column (and, with zero_row, a zero row).
 __global__ void chol_kernel(const zd *__restrict__ A, int lda, int k, zd *__restrict__ Lout, int ldl, double tol,
-                            int zero_row, int *dead, int *status, int flag_rank) {
-  extern __shared__ zd Ls[];   // k x k, ld = k
-  __shared__ double maxdiag;
-  __shared__ int ndead;
-  const int t = threadIdx.x;
-  for (int e = t; e < k * k; e += blockDim.x) {
+                            int zero_row, int *dead, int *status, int flag_rank, const zd *__restrict__ ref, int ldref) {
+  extern __shared__ zd Ls[];   // k x k, ld = k (lower part used)
+  __shared__ double maxdiag, piv;
+  __shared__ int isdead, ndead;
+  const int t = threadIdx.x, nt = blockDim.x;
+  for (int e = t; e < k * k; e += nt) {
     const int i = e % k, j = e / k;
     Ls[e] = (i >= j) ? A[(size_t)j * lda + i] : mk<double>(0, 0);
   }
-  if (t == 0) {
+  if (t < 32) {
     double m = 0.0;
-    for (int i = 0; i < k; ++i) m = fmax(m, A[(size_t)i * lda + i].re);
-    maxdiag = m;
-    ndead = 0;
+    for (int i = t; i < k; i += 32) m = fmax(m, A[(size_t)i * lda + i].re);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (t == 0) { maxdiag = m; ndead = 0; }
   }
   __syncthreads();
   for (int j = 0; j < k; ++j) {
-    // v_i = A[i][j] - sum_{m<j} L[i][m] conj(L[j][m]) for i >= j
-    zd v = mk<double>(0, 0);
-    const int i = j + t;
-    if (i < k) {
-      v = Ls[j * k + i];
-      for (int m = 0; m < j; ++m) v = v - Ls[m * k + i] * conj(Ls[m * k + j]);
-    }
-    __syncthreads();
-    __shared__ double piv;
-    __shared__ int isdead;
     if (t == 0) {
-      piv = v.re;
-      isdead = !(piv > tol * maxdiag) || !isfinite(piv) || maxdiag <= 0.0;
+      piv = Ls[j * k + j].re;
+      const double refj = ref ? ref[(size_t)j * ldref + j].re : maxdiag;
+      isdead = !(piv > tol * refj) || !isfinite(piv) || !(refj > 0.0);
       if (isdead) ndead++;
+      if (dead) dead[j] = isdead;
     }
     __syncthreads();
-    if (i < k) {
-      if (isdead) {
-        Ls[j * k + i] = (i == j) ? mk<double>(1, 0) : mk<double>(0, 0);
-      } else {
-        const double d = sqrt(piv);
-        Ls[j * k + i] = (i == j) ? mk<double>(d, 0) : zdiv_real(v, d);
+    const double d = isdead ? 1.0 : sqrt(piv);
+    const double inv = 1.0 / d;
+    for (int i = j + t; i < k; i += nt) {
+      if (isdead) Ls[j * k + i] = (i == j) ? mk<double>(1, 0) : mk<double>(0, 0);
+      else Ls[j * k + i] = (i == j) ? mk<double>(d, 0) : mk<double>(Ls[j * k + i].re * inv, Ls[j * k + i].im * inv);
+    }
+    if (isdead && zero_row)
+      for (int m = t; m < j; m += nt) Ls[m * k + j] = mk<double>(0, 0);
+    __syncthreads();
+    if (!isdead) {
+      // trailing update: A[i][c] -= L[i][j] conj(L[c][j]) for j < c <= i
+      const int nrem = k - j - 1;
+      for (int e = t; e < nrem * nrem; e += nt) {
+        const int i = j + 1 + e % nrem, cc = j + 1 + e / nrem;
+        if (i >= cc) Ls[cc * k + i] = Ls[cc * k + i] - Ls[j * k + i] * conj(Ls[j * k + cc]);
       }
     }
-    if (isdead && zero_row && t < j) Ls[t * k + j] = mk<double>(0, 0);
-    if (dead && t == 0) dead[j] = isdead;
     __syncthreads();
   }
-  for (int e = t; e < k * k; e += blockDim.x) {
+  for (int e = t; e < k * k; e += nt) {
     const int i = e % k, j = e / k;
-    Lout[(size_t)j * ldl + i] = Ls[e];
+    Lout[(size_t)j * ldl + i] = (i >= j) ? Ls[e] : mk<double>(0, 0);
   }
   if (t == 0 && ndead > 0 && flag_rank && status) atomicOr(status, ST_RANK);
 }
 
 void sm_chol(const zd *A, int lda, int k, zd *L, int ldl, double tol, int zero_row, int *dead, int *status,
-             int flag_rank, cudaStream_t st) {
-  chol_kernel<<<1, 64, (size_t)k * k * sizeof(zd), st>>>(A, lda, k, L, ldl, tol, zero_row, dead, status, flag_rank);
+             int flag_rank, cudaStream_t st, const zd *ref, int ldref) {
+  ::lrei::count_launch();
+  chol_kernel<<<1, 256, (size_t)k * k * sizeof(zd), st>>>(A, lda, k, L, ldl, tol, zero_row, dead, status, flag_rank,
+                                                          ref, ldref);
 }
 
 // --------------------------------------------------------------- Jacobi
@@ -339,12 +366,12 @@ void sm_jacobi(bool fp64, const zd *A, int lda, int k, zd *U, int ldu, double *w
   if (fp64) {
     const bool in_smem = jacobi_smem<double>(k, true) <= lim;
     const size_t bytes = jacobi_smem<double>(k, in_smem);
-    jacobi_kernel<double><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<double> *)scratch,
+    ::lrei::count_launch(); jacobi_kernel<double><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<double> *)scratch,
                                                  max_sweeps, tol, status);
   } else {
     const bool in_smem = jacobi_smem<float>(k, true) <= lim;
     const size_t bytes = jacobi_smem<float>(k, in_smem);
-    jacobi_kernel<float><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
+    ::lrei::count_launch(); jacobi_kernel<float><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
                                                 max_sweeps, tol, status);
   }
 }
@@ -408,7 +435,8 @@ size_t sm_eig_ws_bytes(int kmax, int rmax) {
   b += 4 * (size_t)kmax * rmax * z;  // W1, A21, E1, W2
   b += 4 * (size_t)rmax * rmax * z;  // G1, L1, Ar, Wr
   b += sm_jacobi_scratch_bytes(kmax);
-  return b + 1024;
+  b += (size_t)rmax * rmax * z + (size_t)kmax * rmax * z;
+  return b + 4096;
 }
 
 void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu, void *ws, int *status,
@@ -426,29 +454,31 @@ void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu,
   zd *Ar = (zd *)take((size_t)r * r * sizeof(zd));
   zd *Wr = (zd *)take((size_t)r * r * sizeof(zd));
   void *jscratch = take(sm_jacobi_scratch_bytes(k));
+  zd *Inv = (zd *)take((size_t)r * r * sizeof(zd));
+  zd *Xc = (zd *)take((size_t)k * r * sizeof(zd));
   const zd one = mk<double>(1, 0), zero = mk<double>(0, 0);
   // 1. FP32 eigendecomposition of the whole k x k matrix
-  sm_jacobi(false, M, ldm, k, U, k, w, jscratch, 20, 1e-6, nullptr, st);
+  sm_jacobi(false, M, ldm, k, U, k, w, jscratch, 12, 1e-5, nullptr, st);
   // 2.-3. block-Newton corrections of the top-r invariant subspace, each followed by an
   // FP64 Cholesky-QR re-orthonormalisation of E1
   sm_copy(U, k, k, r, E1, k, st);
   const zd mone = mk<double>(-1, 0);
-  const int passes = (k > r) ? 3 : 1;
+  const int passes = (k > r) ? 4 : 1;
   for (int it = 0; it < passes; ++it) {
     if (k > r) {
       sm_gemm('N', 'N', k, r, k, one, M, ldm, E1, k, zero, W1, k, st);           // W1 = M E
       sm_gemm('C', 'N', r, r, k, one, E1, k, W1, k, zero, Ar, r, st);            // A11 = E^H M E
       sm_gemm('N', 'N', k, r, r, mone, E1, k, Ar, r, one, W1, k, st);           // R = M E - E A11
       sm_gemm('C', 'N', k - r, r, k, one, U + (size_t)r * k, k, W1, k, zero, A21, k, st);   // Ur^H R
-      newton_scale_kernel<<<r, 64, 0, st>>>(A21, k, Ar, r, w, k);               // X
+      ::lrei::count_launch(); newton_scale_kernel<<<r, 64, 0, st>>>(A21, k, Ar, r, w, k);               // X
       sm_gemm('N', 'N', k, r, k - r, one, U + (size_t)r * k, k, A21, k, zero, W2, k, st);    // D = Ur X
       sm_gemm('C', 'N', r, r, k, one, E1, k, W2, k, zero, G1, r, st);            // E^H D
       sm_gemm('N', 'N', k, r, r, mone, E1, k, G1, r, one, W2, k, st);           // D -= E (E^H D)
-      add_kernel<<<8, 256, 0, st>>>(E1, k, W2, k, k, r);                        // E += D
+      ::lrei::count_launch(); add_kernel<<<8, 256, 0, st>>>(E1, k, W2, k, k, r);                        // E += D
     }
     sm_gemm('C', 'N', r, r, k, one, E1, k, E1, k, zero, G1, r, st);
-    sm_chol(G1, r, r, L1, r, 0.0, 0, nullptr, nullptr, 0, st);
-    sm_rtrsm_lh(E1, k, k, L1, r, r, st);
+    sm_chol(G1, r, r, L1, r, 0.0, 0, nullptr, nullptr, 0, st, nullptr, 0);
+    sm_rtrsm_lh_ws(E1, k, k, L1, r, r, Inv, Xc, st);
   }
   // 4. Rayleigh-Ritz on span(E1) in FP64
   sm_gemm('N', 'N', k, r, k, one, M, ldm, E1, k, zero, W2, k, st);
@@ -458,7 +488,7 @@ void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu,
   sm_gemm('N', 'N', k, r, r, one, E1, k, Wr, r, zero, Y, ldy, st);
   // 5. residual check of the returned pairs
   sm_gemm('N', 'N', k, r, k, one, M, ldm, Y, ldy, zero, W1, k, st);
-  eig_check_kernel<<<1, 256, 0, st>>>(W1, k, Y, ldy, mu, k, r, 1e-9, status);
+  ::lrei::count_launch(); eig_check_kernel<<<1, 256, 0, st>>>(W1, k, Y, ldy, mu, k, r, 1e-9, status);
 }
 
 // ------------------------------------------------------------ elementwise
@@ -473,16 +503,16 @@ __global__ void copy_kernel(const zd *A, int lda, int M, int N, zd *B, int ldb, 
 }
 static int grid_for(long long n) { long long g = (n + 255) / 256; return (int)(g < 1 ? 1 : (g > 1024 ? 1024 : g)); }
 void sm_copy(const zd *A, int lda, int M, int N, zd *B, int ldb, cudaStream_t st) {
-  copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, B, ldb, 0);
+  ::lrei::count_launch(); copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, B, ldb, 0);
 }
 void sm_conj_transpose(const zd *A, int lda, int M, int N, zd *B, int ldb, cudaStream_t st) {
-  copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, B, ldb, 1);
+  ::lrei::count_launch(); copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, B, ldb, 1);
 }
 void sm_zero(zd *A, int lda, int M, int N, cudaStream_t st) {
-  copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(nullptr, 0, M, N, A, lda, 2);
+  ::lrei::count_launch(); copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(nullptr, 0, M, N, A, lda, 2);
 }
 void sm_set_identity(zd *A, int lda, int M, int N, cudaStream_t st) {
-  copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(nullptr, 0, M, N, A, lda, 3);
+  ::lrei::count_launch(); copy_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(nullptr, 0, M, N, A, lda, 3);
 }
 
 __global__ void hermitize_kernel(zd *A, int lda, int k) {
@@ -496,7 +526,7 @@ __global__ void hermitize_kernel(zd *A, int lda, int k) {
     if (i == j) A[(size_t)j * lda + i] = mk<double>(h.re, 0);
   }
 }
-void sm_hermitize(zd *A, int lda, int k, cudaStream_t st) { hermitize_kernel<<<grid_for((long long)k * k), 256, 0, st>>>(A, lda, k); }
+void sm_hermitize(zd *A, int lda, int k, cudaStream_t st) { ::lrei::count_launch(); hermitize_kernel<<<grid_for((long long)k * k), 256, 0, st>>>(A, lda, k); }
 
 __global__ void scale_kernel(zd *A, int lda, int M, int N, double s) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x) {
@@ -505,7 +535,7 @@ __global__ void scale_kernel(zd *A, int lda, int M, int N, double s) {
   }
 }
 void sm_scale_cols(zd *A, int lda, int M, int N, double s, cudaStream_t st) {
-  scale_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, s);
+  ::lrei::count_launch(); scale_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, s);
 }
 
 __global__ void store_gram_cols_kernel(const zd *R, int ldr, int k, int r, zd *G, int ldg) {
@@ -518,7 +548,7 @@ __global__ void store_gram_cols_kernel(const zd *R, int ldr, int k, int r, zd *G
   }
 }
 void sm_store_gram_cols(const zd *R, int ldr, int k, int r, zd *G, int ldg, cudaStream_t st) {
-  store_gram_cols_kernel<<<grid_for((long long)(k + r) * r), 256, 0, st>>>(R, ldr, k, r, G, ldg);
+  ::lrei::count_launch(); store_gram_cols_kernel<<<grid_for((long long)(k + r) * r), 256, 0, st>>>(R, ldr, k, r, G, ldg);
 }
 
 }  // namespace lrei
@@ -526,6 +556,7 @@ void sm_store_gram_cols(const zd *R, int ldr, int k, int r, zd *G, int ldg, cuda
 namespace lrei {
 int sm_init() {
   const int lim = 210 * 1024;
+  cudaFuncSetAttribute(trsv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t a = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t b = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return (a == cudaSuccess && b == cudaSuccess) ? 0 : -1;

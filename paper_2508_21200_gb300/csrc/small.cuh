@@ -18,13 +18,15 @@ void sm_trsv(char op, const zd *L, int ldl, int k, zd *B, int ldb, int ncols, cu
 
 // Rows of X (nrows x k): X <- X (L^H)^{-1}, L lower triangular k x k.
 void sm_rtrsm_lh(zd *X, int ldx, int nrows, const zd *L, int ldl, int k, cudaStream_t st);
+// Same through an explicit inverse and one GEMM; inv: k x k scratch, xcopy: nrows x k scratch.
+void sm_rtrsm_lh_ws(zd *X, int ldx, int nrows, const zd *L, int ldl, int k, zd *inv, zd *xcopy, cudaStream_t st);
 
 // Cholesky A = L L^H of a Hermitian k x k matrix (k <= 64), one CTA.  A pivot below
 // tol * max_i A_ii marks column j dead: L[j][j] = 1 and the rest of column j zero; with
 // zero_row also row j of L (left of the diagonal) is zeroed.  dead (k ints) may be NULL.
 // Nonzero status bit ST_RANK is set when any column is dead and flag_rank is 1.
 void sm_chol(const zd *A, int lda, int k, zd *L, int ldl, double tol, int zero_row, int *dead, int *status,
-             int flag_rank, cudaStream_t st);
+             int flag_rank, cudaStream_t st, const zd *ref = nullptr, int ldref = 0);
 
 // Hermitian eigendecomposition by cyclic Jacobi in working precision T (float or double),
 // one CTA.  Eigenvalues w sorted decreasing (ties by index), eigenvectors U (k x k, FP64).

@@ -16,6 +16,8 @@
 // (complex64 path, TwoSum), written out as FP64 partials.
 #include "tsk.cuh"
 
+#include <cstdlib>
+
 namespace lrei {
 
 // ---------------------------------------------------------------- loads
@@ -133,6 +135,8 @@ template <> struct Acc<float> {
 
 // ------------------------------------------------------ fused tile pass
 constexpr int TS_THREADS = 256;
+static bool g_force_v1 = false;   // selects the unblocked kernel (A/B comparison)
+
 
 template <typename T>
 struct TSLayout {
@@ -249,6 +253,216 @@ __global__ void __launch_bounds__(TS_THREADS) ts_kernel(const __grid_constant__ 
   }
 }
 
+// ------------------------------------------------ fused tile pass, register-blocked
+// Same contract as ts_kernel.  Shared tiles use a padded row stride RS (complex elements) so
+// that rows of a tile fall in different banks.  The Gram is computed by MI x MJ register
+// micro-tiles (rows (m, i) of [q_0..q_{gl-1}, G], columns j), split over `nph` phases of the
+// tile rows; per-thread partials are flushed every FLUSH tiles into per-thread accumulators
+// in shared memory (compensated FP32 pairs or FP64), then reduced over phases at the end.
+// The new tile is a small GEMM [q_0..q_{nq-1}, S] (tr x (nq+1) rp) x coef ((nq+1) rp x rp),
+// one row x 4 columns per thread.
+template <typename T> struct TS2 {
+  static constexpr int MI = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int MJ = 4;
+  static constexpr int PAD = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int FLUSH = sizeof(T) == 4 ? 4 : 1 << 30;
+};
+
+__host__ __device__ inline int ts2_rp(int r) { return (r + 3) & ~3; }
+
+template <typename T>
+__host__ __device__ inline size_t ts2_bytes(int nq, int gl, int r, int tr, int mode, int mt) {
+  const int rp = ts2_rp(r), RS = rp + TS2<T>::PAD;
+  size_t b = ((size_t)nq * tr * RS + 2 * (size_t)tr * RS) * sizeof(cx<T>);
+  if (mode != 0) b += (size_t)(nq + 1) * rp * rp * sizeof(cx<T>);
+  b += (size_t)TS_THREADS * mt * TS2<T>::MI * TS2<T>::MJ * 16;   // per-thread accumulators
+  return b;
+}
+
+template <typename T, int CPT, int MT>
+__global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__ ModelArgs M,
+                                                        const __grid_constant__ TSArgs a, int tr,
+                                                        const cx<T> *__restrict__ coefg) {
+  constexpr int MI = TS2<T>::MI, MJ = TS2<T>::MJ;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int r = a.r, nq = a.nq, gl = a.gram_left;
+  const int rp = ts2_rp(r), RS = rp + TS2<T>::PAD;
+  const int tid = threadIdx.x;
+  cx<T> *qs = reinterpret_cast<cx<T> *>(smem);
+  cx<T> *gs = qs + (size_t)nq * tr * RS;
+  cx<T> *ns = gs + (size_t)tr * RS;
+  cx<T> *cs = ns + (size_t)tr * RS;
+  const int ncoef = (a.mode != 0) ? (nq + 1) * rp * rp : 0;
+  double *slots = reinterpret_cast<double *>(cs + ncoef);   // [TS_THREADS][MT][MI*MJ] x 16 bytes
+
+  for (int e = tid; e < ncoef; e += TS_THREADS) cs[e] = coefg[e];
+  for (int e = tid; e < TS_THREADS * MT * MI * MJ * 2; e += TS_THREADS) slots[e] = 0.0;
+
+  // Gram micro-tile assignment
+  const int nI = (gl + 1) * rp / MI, nJ = rp / MJ, NMT = nI * nJ;
+  const int nph = (MT == 1 && NMT < TS_THREADS) ? TS_THREADS / NMT : 1;
+  const int ph = (MT == 1) ? tid / NMT : 0;
+  int mts[MT];
+  bool mval[MT];
+#pragma unroll
+  for (int u = 0; u < MT; ++u) {
+    mts[u] = (MT == 1) ? tid % NMT : tid + u * TS_THREADS;
+    mval[u] = (MT == 1) ? (ph < nph) : (mts[u] < NMT);
+  }
+  cx<T> acc[MT][MI][MJ];
+#pragma unroll
+  for (int u = 0; u < MT; ++u)
+#pragma unroll
+    for (int x = 0; x < MI; ++x)
+#pragma unroll
+      for (int y = 0; y < MJ; ++y) acc[u][x][y] = mk<T>(0, 0);
+  __syncthreads();
+
+  const long long ntiles = (a.N + tr - 1) / tr;
+  const int gpr = r / CPT;
+  int since_flush = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row0 = tile * tr;
+    const int rows = (int)((a.N - row0) < tr ? (a.N - row0) : tr);
+    // S tile
+    if (a.mode != 2) {
+      const cx<T> *src = reinterpret_cast<const cx<T> *>(a.src);
+      for (int e = tid; e < tr * gpr; e += TS_THREADS) {
+        const int lr = e / gpr, c0 = (e % gpr) * CPT;
+        cx<T> v[CPT];
+        if (lr < rows) {
+          if (a.apply_h) hv_group<T, CPT>(M, src, r, (uint32_t)(row0 + lr), c0, v);
+          else Group<T, CPT>::load(src + (size_t)(row0 + lr) * r + c0, v);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CPT; ++c) v[c] = mk<T>(0, 0);
+        }
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) gs[lr * RS + c0 + c] = v[c];
+      }
+      if (rp > r)
+        for (int e = tid; e < tr * (rp - r); e += TS_THREADS) gs[(e / (rp - r)) * RS + r + e % (rp - r)] = mk<T>(0, 0);
+    }
+    // Q tiles (rows of one block are contiguous in global memory)
+    for (int m = 0; m < nq; ++m) {
+      const cx<T> *qm = reinterpret_cast<const cx<T> *>(a.q[m]) + (size_t)row0 * r;
+      cx<T> *dst = qs + (size_t)m * tr * RS;
+      for (int e = tid; e < tr * rp; e += TS_THREADS) {
+        const int lr = e / rp, c = e % rp;
+        dst[lr * RS + c] = (lr < rows && c < r) ? ldg1(qm + (size_t)lr * r + c) : mk<T>(0, 0);
+      }
+    }
+    __syncthreads();
+    const cx<T> *G = gs;
+    if (a.mode != 0) {
+      cx<T> *out = reinterpret_cast<cx<T> *>(a.out);
+      const int ngrp = rp / 4;
+      for (int e = tid; e < tr * ngrp; e += TS_THREADS) {
+        const int lr = e / ngrp, j0 = (e % ngrp) * 4;
+        cx<T> o[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o[y] = mk<T>(0, 0);
+        const int mlast = (a.mode == 1) ? nq : nq - 1;
+        for (int m = 0; m <= mlast; ++m) {
+          const cx<T> *X = (m < nq) ? qs + (size_t)m * tr * RS + lr * RS : gs + lr * RS;
+          const cx<T> *C = cs + (size_t)m * rp * rp + j0;
+          for (int i = 0; i < r; ++i) {
+            const cx<T> x = X[i];
+            const cx<T> *ci = C + i * rp;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) fma_(o[y], x, ci[y]);
+          }
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int j = j0 + y;
+          const cx<T> v = (lr < rows && j < r) ? o[y] : mk<T>(0, 0);
+          ns[lr * RS + j] = v;
+          if (lr < rows && j < r && out) out[(size_t)(row0 + lr) * r + j] = v;
+        }
+      }
+      __syncthreads();
+      G = ns;
+    } else if (a.out) {
+      cx<T> *out = reinterpret_cast<cx<T> *>(a.out);
+      for (int e = tid; e < rows * r; e += TS_THREADS) out[(size_t)row0 * r + e] = gs[(e / r) * RS + e % r];
+    }
+    // Gram micro-tiles
+#pragma unroll
+    for (int u = 0; u < MT; ++u) {
+      if (!mval[u]) continue;
+      const int I = mts[u] / nJ, J = mts[u] % nJ;
+      const int i0 = I * MI, m = i0 / rp, ii0 = i0 % rp, j0 = J * MJ;
+      const cx<T> *L = (m < gl) ? qs + (size_t)m * tr * RS : G;
+      for (int lr = ph; lr < tr; lr += nph) {
+        cx<T> lv[MI], gv[MJ];
+#pragma unroll
+        for (int x = 0; x < MI; ++x) lv[x] = L[lr * RS + ii0 + x];
+#pragma unroll
+        for (int y = 0; y < MJ; ++y) gv[y] = G[lr * RS + j0 + y];
+#pragma unroll
+        for (int x = 0; x < MI; ++x)
+#pragma unroll
+          for (int y = 0; y < MJ; ++y) fmac_(acc[u][x][y], lv[x], gv[y]);
+      }
+    }
+    if (++since_flush >= TS2<T>::FLUSH) {
+      since_flush = 0;
+#pragma unroll
+      for (int u = 0; u < MT; ++u)
+#pragma unroll
+        for (int x = 0; x < MI; ++x)
+#pragma unroll
+          for (int y = 0; y < MJ; ++y) {
+            Acc<T>::add(slots, (tid * MT + u) * MI * MJ + x * MJ + y, acc[u][x][y]);
+            acc[u][x][y] = mk<T>(0, 0);
+          }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < MT; ++u)
+#pragma unroll
+    for (int x = 0; x < MI; ++x)
+#pragma unroll
+      for (int y = 0; y < MJ; ++y) Acc<T>::add(slots, (tid * MT + u) * MI * MJ + x * MJ + y, acc[u][x][y]);
+  __syncthreads();
+  // reduce over phases and write the CTA partial in the column-major ((gl+1) r) x r layout
+  const int ldg_ = (gl + 1) * r, nent = ldg_ * r;
+  double *outp = a.partial + (size_t)blockIdx.x * nent * 2;
+  for (int e = tid; e < nent; e += TS_THREADS) {
+    const int j = e / ldg_, row = e % ldg_, m = row / r, i = row % r;
+    const int ic = m * rp + i;                          // row in the padded concatenation
+    const int I = ic / MI, x = ic % MI, J = j / MJ, y = j % MJ;
+    const int mt = I * nJ + J;
+    cx<double> sum = mk<double>(0, 0);
+    if (MT == 1) {
+      for (int p = 0; p < nph; ++p) sum = sum + Acc<T>::get(slots, (p * NMT + mt) * MI * MJ + x * MJ + y);
+    } else {
+      const int owner = mt % TS_THREADS, u = mt / TS_THREADS;
+      sum = Acc<T>::get(slots, (owner * MT + u) * MI * MJ + x * MJ + y);
+    }
+    outp[2 * e] = sum.re;
+    outp[2 * e + 1] = sum.im;
+  }
+}
+
+// Coefficients in the padded row-major layout of ts2_kernel: row m*rp + i, column j.
+template <typename T>
+__global__ void coef_convert2_kernel(const zd *coefQ, const zd *coefS, int nq, int r, int mode, cx<T> *out) {
+  const int rp = ts2_rp(r);
+  const int rows = (nq + 1) * rp;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * rp; e += gridDim.x * blockDim.x) {
+    const int row = e / rp, j = e % rp, m = row / rp, i = row % rp;
+    zd v = mk<double>(0, 0);
+    if (i < r && j < r) {
+      if (m < nq) v = coefQ ? coefQ[(size_t)j * nq * r + m * r + i] : mk<double>(0, 0);
+      else if (mode == 1 && coefS) v = coefS[(size_t)j * r + i];
+    }
+    out[e] = mk<T>((T)v.re, (T)v.im);
+  }
+}
+
 template <typename T>
 __global__ void coef_convert_kernel(const zd *coefQ, const zd *coefS, int nq, int r, int mode, cx<T> *out) {
   const int ldc = (nq + 1) * r;
@@ -267,9 +481,13 @@ __global__ void coef_convert_kernel(const zd *coefQ, const zd *coefS, int nq, in
 
 __global__ void reduce_kernel(const double *__restrict__ part, int nparts, int len, double *__restrict__ out) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < len; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int p = 0; p < nparts; ++p) s += part[(size_t)p * len + e];
-    out[e] = s;
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int p = 0;
+    for (; p + 8 <= nparts; p += 8)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[u] += part[(size_t)(p + u) * len + e];
+    for (; p < nparts; ++p) s[0] += part[(size_t)p * len + e];
+    out[e] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
   }
 }
 
@@ -277,7 +495,7 @@ int ts_max_grid(int nsm) { return 2 * nsm; }
 size_t ts_partial_doubles(int gram_left, int r) { return (size_t)(gram_left + 1) * r * r * 2; }
 
 template <typename T>
-static int launch_ts_t(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_t st) {
+static int launch_ts_v1(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_t st) {
   const int r = a.r;
   // choose tile rows / coefficient placement so the CTA fits in shared memory
   const size_t budget = 200 * 1024;
@@ -295,7 +513,7 @@ static int launch_ts_t(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_
   if (a.mode != 0) {
     if (!a.coef_scratch) return -1;
     coefg = reinterpret_cast<cx<T> *>(a.coef_scratch);
-    coef_convert_kernel<T><<<8, 256, 0, st>>>(a.coefQ, a.coefS, a.nq, r, a.mode, coefg);
+    ::lrei::count_launch(); coef_convert_kernel<T><<<8, 256, 0, st>>>(a.coefQ, a.coefS, a.nq, r, a.mode, coefg);
   }
   const long long ntiles = (a.N + tr - 1) / tr;
   int grid = (int)(ntiles < (long long)ts_max_grid(nsm) ? ntiles : ts_max_grid(nsm));
@@ -305,10 +523,49 @@ static int launch_ts_t(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_
   int cpt = 1;
   if (r % cpt_max == 0) cpt = cpt_max;
   else if (r % 2 == 0) cpt = 2;
-  auto go = [&](auto kern) { kern<<<grid, TS_THREADS, bytes, st>>>(M, a, tr, coef_smem ? 1 : 0, coefg); };
+  auto go = [&](auto kern) { ::lrei::count_launch(); kern<<<grid, TS_THREADS, bytes, st>>>(M, a, tr, coef_smem ? 1 : 0, coefg); };
   if (cpt == 4) go(ts_kernel<T, (sizeof(T) == 4 ? 4 : 2)>);
   else if (cpt == 2) go(ts_kernel<T, 2>);
   else go(ts_kernel<T, 1>);
+  return grid;
+}
+
+template <typename T>
+static int launch_ts_t(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_t st) {
+  const int r = a.r, rp = ts2_rp(r);
+  const int NMT = (a.gram_left + 1) * rp / TS2<T>::MI * (rp / TS2<T>::MJ);
+  const int mt = NMT <= TS_THREADS ? 1 : (NMT <= 2 * TS_THREADS ? 2 : 0);
+  const size_t budget = 200 * 1024;
+  int tr = 64;
+  if (mt > 0)
+    while (tr > 8 && ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt) > budget) tr /= 2;
+  if (mt == 0 || ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt) > budget || g_force_v1)
+    return launch_ts_v1<T>(M, a, nsm, st);
+  const size_t bytes = ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt);
+  cx<T> *coefg = nullptr;
+  if (a.mode != 0) {
+    if (!a.coef_scratch) return -1;
+    coefg = reinterpret_cast<cx<T> *>(a.coef_scratch);
+    ::lrei::count_launch();
+    coef_convert2_kernel<T><<<8, 256, 0, st>>>(a.coefQ, a.coefS, a.nq, r, a.mode, coefg);
+  }
+  const long long ntiles = (a.N + tr - 1) / tr;
+  int grid = (int)(ntiles < (long long)ts_max_grid(nsm) ? ntiles : ts_max_grid(nsm));
+  if (grid < 1) grid = 1;
+  const int cpt_max = sizeof(T) == 4 ? 4 : 2;
+  int cpt = 1;
+  if (r % cpt_max == 0) cpt = cpt_max;
+  else if (r % 2 == 0) cpt = 2;
+  auto go = [&](auto kern) { ::lrei::count_launch(); kern<<<grid, TS_THREADS, bytes, st>>>(M, a, tr, coefg); };
+  if (mt == 1) {
+    if (cpt == cpt_max && cpt_max == 4) go(ts2_kernel<T, (sizeof(T) == 4 ? 4 : 2), 1>);
+    else if (cpt == 2) go(ts2_kernel<T, 2, 1>);
+    else go(ts2_kernel<T, 1, 1>);
+  } else {
+    if (cpt == cpt_max && cpt_max == 4) go(ts2_kernel<T, (sizeof(T) == 4 ? 4 : 2), 2>);
+    else if (cpt == 2) go(ts2_kernel<T, 2, 2>);
+    else go(ts2_kernel<T, 1, 2>);
+  }
   return grid;
 }
 
@@ -317,10 +574,39 @@ int launch_ts(bool fp64, const ModelArgs &M, const TSArgs &a, int nsm, cudaStrea
   return fp64 ? launch_ts_t<double>(M, a, nsm, st) : launch_ts_t<float>(M, a, nsm, st);
 }
 
+// Two-stage deterministic reduction: CTAs (entry chunk, part slice) sum a fixed slice of parts,
+// then one pass sums the slices in order.
+__global__ void reduce_slices_kernel(const double *__restrict__ part, int nparts, int len, int nslice,
+                                     double *__restrict__ tmp) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sl = blockIdx.y;
+  if (e >= len) return;
+  const int per = (nparts + nslice - 1) / nslice;
+  const int p0 = sl * per, p1 = min(nparts, p0 + per);
+  double s[4] = {0, 0, 0, 0};
+  int p = p0;
+  for (; p + 4 <= p1; p += 4)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s[u] += part[(size_t)(p + u) * len + e];
+  for (; p < p1; ++p) s[0] += part[(size_t)p * len + e];
+  tmp[(size_t)sl * len + e] = (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 void launch_reduce(const double *partial, int nparts, int len_doubles, double *out, cudaStream_t st) {
-  int blocks = (len_doubles + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  reduce_kernel<<<blocks, 256, 0, st>>>(partial, nparts, len_doubles, out);
+  const int nslice = nparts >= 64 ? 16 : 1;
+  if (nslice == 1) {
+    int blocks = (len_doubles + 255) / 256;
+    ::lrei::count_launch();
+    reduce_kernel<<<blocks, 256, 0, st>>>(partial, nparts, len_doubles, out);
+    return;
+  }
+  // the slices live after the partials of the largest grid (ts_max_grid(nsm) parts), which the
+  // caller sized with room for nslice extra rows
+  double *tmp = const_cast<double *>(partial) + (size_t)nparts * len_doubles;
+  dim3 g((len_doubles + 127) / 128, nslice);
+  ::lrei::count_launch(2);
+  reduce_slices_kernel<<<g, 128, 0, st>>>(partial, nparts, len_doubles, nslice, tmp);
+  reduce_kernel<<<(len_doubles + 255) / 256, 256, 0, st>>>(tmp, nslice, len_doubles, out);
 }
 
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st) {
@@ -332,13 +618,13 @@ void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long 
   };
   if (fp64) {
     using T = double;
-    if (r % 2 == 0) hv_kernel<T, 2><<<grid_for(2), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r);
-    else hv_kernel<T, 1><<<grid_for(1), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r);
+    if (r % 2 == 0) { ::lrei::count_launch(); hv_kernel<T, 2><<<grid_for(2), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r); }
+    else { ::lrei::count_launch(); hv_kernel<T, 1><<<grid_for(1), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r); }
   } else {
     using T = float;
-    if (r % 4 == 0) hv_kernel<T, 4><<<grid_for(4), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r);
-    else if (r % 2 == 0) hv_kernel<T, 2><<<grid_for(2), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r);
-    else hv_kernel<T, 1><<<grid_for(1), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r);
+    if (r % 4 == 0) { ::lrei::count_launch(); hv_kernel<T, 4><<<grid_for(4), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r); }
+    else if (r % 2 == 0) { ::lrei::count_launch(); hv_kernel<T, 2><<<grid_for(2), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r); }
+    else { ::lrei::count_launch(); hv_kernel<T, 1><<<grid_for(1), 256, 0, st>>>(M, (const cx<T> *)X, (cx<T> *)Y, N, r); }
   }
 }
 
@@ -416,10 +702,10 @@ int launch_obs(bool fp64, const ModelArgs &M, const void *V, long long N, int r,
   const size_t nent = (size_t)OBS_BLOCKS * r * r;
   if (fp64) {
     size_t bytes = 5 * (size_t)tr * r * sizeof(cx<double>) + nent * 16;
-    obs_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)V, N, r, tr, partial);
+    ::lrei::count_launch(); obs_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)V, N, r, tr, partial);
   } else {
     size_t bytes = 5 * (size_t)tr * r * sizeof(cx<float>) + nent * 16;
-    obs_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)V, N, r, tr, partial);
+    ::lrei::count_launch(); obs_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)V, N, r, tr, partial);
   }
   return grid;
 }
@@ -443,11 +729,11 @@ void launch_convert(const void *src, int src_c64, int ld, void *dst, int dst_fp6
   int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
   if (grid < 1) grid = 1;
   if (src_c64) {
-    if (dst_fp64) convert_kernel<float, double><<<grid, 256, 0, st>>>((const cx<float> *)src, ld, (cx<double> *)dst, N, r);
-    else convert_kernel<float, float><<<grid, 256, 0, st>>>((const cx<float> *)src, ld, (cx<float> *)dst, N, r);
+    if (dst_fp64) { ::lrei::count_launch(); convert_kernel<float, double><<<grid, 256, 0, st>>>((const cx<float> *)src, ld, (cx<double> *)dst, N, r); }
+    else { ::lrei::count_launch(); convert_kernel<float, float><<<grid, 256, 0, st>>>((const cx<float> *)src, ld, (cx<float> *)dst, N, r); }
   } else {
-    if (dst_fp64) convert_kernel<double, double><<<grid, 256, 0, st>>>((const cx<double> *)src, ld, (cx<double> *)dst, N, r);
-    else convert_kernel<double, float><<<grid, 256, 0, st>>>((const cx<double> *)src, ld, (cx<float> *)dst, N, r);
+    if (dst_fp64) { ::lrei::count_launch(); convert_kernel<double, double><<<grid, 256, 0, st>>>((const cx<double> *)src, ld, (cx<double> *)dst, N, r); }
+    else { ::lrei::count_launch(); convert_kernel<double, float><<<grid, 256, 0, st>>>((const cx<double> *)src, ld, (cx<float> *)dst, N, r); }
   }
 }
 
@@ -463,8 +749,8 @@ void launch_check_finite(bool fp64, const void *X, long long N, int r, int *stat
   long long n = N * r * 2;
   int grid = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
   if (grid < 1) grid = 1;
-  if (fp64) finite_kernel<double><<<grid, 256, 0, st>>>((const double *)X, n, status);
-  else finite_kernel<float><<<grid, 256, 0, st>>>((const float *)X, n, status);
+  if (fp64) { ::lrei::count_launch(); finite_kernel<double><<<grid, 256, 0, st>>>((const double *)X, n, status); }
+  else { ::lrei::count_launch(); finite_kernel<float><<<grid, 256, 0, st>>>((const float *)X, n, status); }
 }
 
 }  // namespace lrei
@@ -472,6 +758,7 @@ void launch_check_finite(bool fp64, const void *X, long long N, int r, int *stat
 namespace lrei {
 // Raise the dynamic shared-memory limit of every tile kernel once (outside any stream capture).
 int ts_init() {
+  g_force_v1 = getenv("LREI_TS_V1") != nullptr;
   const int lim = 210 * 1024;
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {
@@ -483,6 +770,16 @@ int ts_init() {
   set((const void *)ts_kernel<float, 4>);
   set((const void *)ts_kernel<float, 2>);
   set((const void *)ts_kernel<float, 1>);
+  set((const void *)ts2_kernel<double, 2, 1>);
+  set((const void *)ts2_kernel<double, 1, 1>);
+  set((const void *)ts2_kernel<double, 2, 2>);
+  set((const void *)ts2_kernel<double, 1, 2>);
+  set((const void *)ts2_kernel<float, 4, 1>);
+  set((const void *)ts2_kernel<float, 2, 1>);
+  set((const void *)ts2_kernel<float, 1, 1>);
+  set((const void *)ts2_kernel<float, 4, 2>);
+  set((const void *)ts2_kernel<float, 2, 2>);
+  set((const void *)ts2_kernel<float, 1, 2>);
   set((const void *)obs_kernel<double>);
   set((const void *)obs_kernel<float>);
   return e == cudaSuccess ? 0 : -1;

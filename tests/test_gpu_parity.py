@@ -296,3 +296,33 @@ def test_config2_n16_fp64_vs_lowrank_oracle(mdl):
     ref = lr.observables(V, w.lam, Hs, M)
     assert obs_err(o, ref, w) <= TOL["fp64"]
     assert np.abs(o["ritz"] - mu).max() <= TOL["fp64"] * w.lam.max()
+
+
+# ------------------------------------------------------------ Adams-Bashforth
+
+@pytest.mark.parametrize("scheme", ["ab2", "ab3", "ab4"])
+@pytest.mark.parametrize("mdl", ["qll", "qllg"])
+def test_ab_matches_dense_ei(scheme, mdl):
+    # AB_m with an RK4 start-up (m-1 steps), periodic anisotropic chain, history kept across calls
+    w = li.workload(2, n=7, r=3)
+    err, err_mu = _trajectory_check(w, "fp64", 40, 8, scheme=scheme, kappa=0.1, mdl=mdl)
+    assert err <= TOL["fp64"] and err_mu <= TOL["fp64"], (err, err_mu)
+
+
+def test_ab3_mixed_matches_dense_ei():
+    w = li.workload(2, n=8, r=4)
+    err, err_mu = _trajectory_check(w, "mixed", 60, 20, scheme="ab3", kappa=0.1, mdl="qll")
+    assert err <= TOL["mixed"] and err_mu <= TOL["mixed"], (err, err_mu)
+
+
+def test_ab_history_resets_on_dt_change():
+    w = li.workload(1, n=6, r=2)
+    H, M = dense_ops(w)
+    L = ctx_for(w, "fp64")
+    L.set_state(dev(w.V), w.lam)
+    L.step(0.01, "ab3", 4)
+    L.step(0.02, "ab3", 3)     # new dt: history restarts with RK4 steps
+    V, _ = de.integrate(w.V, w.lam, H, w.kappa, w.model, 0.01, 4, "ab3")
+    V, _ = de.integrate(V, w.lam, H, w.kappa, w.model, 0.02, 3, "ab3")
+    o, ref = L.observables(), de.observables(V, w.lam, H, M)
+    assert obs_err(o, ref, w) <= TOL["fp64"]

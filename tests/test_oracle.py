@@ -353,3 +353,42 @@ def test_hamiltonian_row_matches_dense():
     H = model.hamiltonian(n, w.bonds, w.B)
     for b in (0, 7, 21, 31):
         assert np.abs(model.hamiltonian_row(n, w.bonds, w.B, b) - H[b]).max() == 0
+
+
+# ------------------------------------------------------- controller network
+
+def test_mlp_gradients_match_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    p = mlp.init_params(7, 2, rng, hidden=16)
+    X = rng.standard_normal((5, 7))
+    T = rng.standard_normal((5, 2))
+    w = np.array([1.0, 0.3])
+    g = mlp.grads(p, X, T, w)
+    eps = 1e-6
+    for k in p:
+        flat = p[k].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + eps
+            lp = mlp.loss(p, X, T, w)
+            flat[idx] = old - eps
+            lm = mlp.loss(p, X, T, w)
+            flat[idx] = old
+            assert abs((lp - lm) / (2 * eps) - g[k].reshape(-1)[idx]) < 1e-8
+
+
+def test_mlp_linear_limit_and_adam_first_step():
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    p = mlp.init_params(3, 1, rng, hidden=8)
+    # with tiny inputs and zero biases the network is linear: y = W3 W2 W1 x to first order
+    X = 1e-6 * rng.standard_normal((4, 3))
+    Y, _ = mlp.forward(p, X)
+    assert np.allclose(Y, X @ (p["W3"] @ p["W2"] @ p["W1"]).T, rtol=1e-9, atol=1e-18)
+    # Adam's first update is -lr * g / (|g| + eps) (bias corrections cancel)
+    g = mlp.grads(p, rng.standard_normal((4, 3)), rng.standard_normal((4, 1)))
+    q = {k: v.copy() for k, v in p.items()}
+    mlp.adam_step(q, g, {}, lr=1e-2)
+    for k in p:
+        assert np.allclose(q[k] - p[k], -1e-2 * g[k] / (np.abs(g[k]) + 1e-8), atol=1e-15)
