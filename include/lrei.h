@@ -150,6 +150,14 @@ int lrei_apply_h(lrei_ctx *ctx, const void *V_dev, void *Y_dev, int r);
 int lrei_rhs(lrei_ctx *ctx, void *Z_dev, void *W_dev, double *G_host,
              int complement);
 
+/* The r Householder reflectors that triangularise the current factor (Sec. 3.4,
+ * eq. Householder-mat) in compact WY form Q = P_1 ... P_r = I - U T U^H:
+ * U (N x r, device, row-major, context dtype, unit lower trapezoidal) into U_dev,
+ * T (r x r upper triangular, complex column-major, 2 r^2 doubles) and D (r complex)
+ * into host arrays, with Q[:, :r] = V diag(D), so the complement of V is Q[:, r:].
+ * Requires r < N. */
+int lrei_householder(lrei_ctx *ctx, void *U_dev, double *T_host, double *D_host);
+
 /* Raw device status bits of the last step / set_state call (diagnostics):
  * 1 non-finite, 2 small eigensolver sweep limit, 4 rank-deficient factor,
  * 8 bounded wait ran out, 16 trace, 32 eigenpair residual above tolerance. */

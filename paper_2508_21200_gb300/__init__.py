@@ -81,6 +81,7 @@ def load_library(path: str | None = None):
         "lrei_error_string": (ctypes.c_char_p, [I]),
         "lrei_apply_h": (I, [P, P, P, I]),
         "lrei_rhs": (I, [P, P, P, ctypes.POINTER(D), I]),
+        "lrei_householder": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "lrei_kernel_launches": (L, [P]),
         "lrei_last_status": (I, [P]),
         "lrei_mlp_create": (I, [I, I, P, P, ctypes.POINTER(P)]),
@@ -204,9 +205,21 @@ class Lrei:
         W = torch.empty_like(Z)
         G = np.zeros(2 * self.r * self.r)
         _check(self._lib.lrei_rhs(self._h, ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(W.data_ptr()),
-                                  G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(complement)))
+                                  G.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(complement)), self._h)
         Gc = (G[0::2] + 1j * G[1::2]).reshape(self.r, self.r).T  # column-major -> row-major
         return Z, W, Gc
+
+    def householder(self):
+        """Compact WY factors (U, T, D) of the current factor's Householder reflectors."""
+        import torch
+        U = torch.empty((self.N, self.r), dtype=self.torch_dtype, device="cuda")
+        T = np.zeros(2 * self.r * self.r)
+        Dd = np.zeros(2 * self.r)
+        _check(self._lib.lrei_householder(self._h, ctypes.c_void_p(U.data_ptr()),
+                                          T.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          Dd.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), self._h)
+        Tc = (T[0::2] + 1j * T[1::2]).reshape(self.r, self.r).T
+        return U, Tc, Dd[0::2] + 1j * Dd[1::2]
 
     def kernel_launches(self):
         return int(self._lib.lrei_kernel_launches(self._h))

@@ -35,6 +35,7 @@ int lrei_mlp_forward_on(lrei_mlp *net, const float *X, int B, float *Y, cudaStre
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 namespace lrei {
@@ -430,6 +431,202 @@ __global__ void dist_kernel(const zd *__restrict__ red, int r, const zd *__restr
   }
 }
 
+// Step-doubling distance without cancellation.  With Vbar = V L^{-H}, Vbar_b = V_b L_b^{-H} and
+// C = Vbar_b^H Vbar, write Vbar = Vbar_b C + P (P orthogonal to V_b).  Then to second order
+//   ||rho - rho_b||_F^2 = ||offdiag(C Lambda C^H)||_F^2 + 2 sum_i lambda_i^2 ||P e_i||^2,
+// where the off-diagonal entries are first-order small (no cancellation) and P is formed
+// explicitly in N-space by one fused pass (coefficients written here).
+__global__ void dist_prep_kernel(const zd *__restrict__ red, int r, const zd *__restrict__ Gb,
+                                 const zd *__restrict__ Lcur, int ldl, const double *__restrict__ lam,
+                                 zd *__restrict__ coef, double *__restrict__ out) {
+  extern __shared__ zd sd[];
+  zd *Lb = sd, *Xb = sd + r * r, *Xc = sd + 2 * r * r, *T = sd + 3 * r * r, *C = sd + 4 * r * r, *Lc = sd + 5 * r * r;
+  const int t = threadIdx.x;
+  const int ldr = 2 * r;   // red rows 0..r-1: V_b^* V
+  for (int e = t; e < r * r; e += blockDim.x) Lc[e] = Lcur[(size_t)(e / r) * ldl + (e % r)];
+  __syncthreads();
+  if (t == 0) chol_inv_small(Gb, r, r, Lb, Xb);
+  if (t == (blockDim.x > 32 ? 32 : 0)) {
+    // Xc = Lc^{-1} from the current factor's Cholesky factor
+    for (int j = 0; j < r; ++j)
+      for (int i = 0; i < r; ++i) {
+        if (i < j) { Xc[j * r + i] = mk<double>(0, 0); continue; }
+        zd v = mk<double>(i == j ? 1.0 : 0.0, 0);
+        for (int m = j; m < i; ++m) v = v - Lc[m * r + i] * Xc[j * r + m];
+        const double d = Lc[i * r + i].re;
+        Xc[j * r + i] = mk<double>(v.re / d, v.im / d);
+      }
+  }
+  __syncthreads();
+  for (int e = t; e < r * r; e += blockDim.x) {   // T = Xb (V_b^* V)
+    const int i = e % r, j = e / r;
+    zd v = mk<double>(0, 0);
+    for (int m = 0; m <= i; ++m) fma_(v, Xb[m * r + i], red[(size_t)j * ldr + m]);
+    T[e] = v;
+  }
+  __syncthreads();
+  for (int e = t; e < r * r; e += blockDim.x) {   // C = T Xc^H
+    const int i = e % r, j = e / r;
+    zd v = mk<double>(0, 0);
+    for (int m = 0; m <= j; ++m) v = v + T[m * r + i] * conj(Xc[m * r + j]);
+    C[e] = v;
+  }
+  __syncthreads();
+  // coefficients of P = V Xc^H - V_b (Xb^H C), column-major (2r x r, ld 2r)
+  for (int e = t; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    coef[(size_t)j * 2 * r + i] = conj(Xc[i * r + j]);                  // (Xc^H)_{ij}
+    zd v = mk<double>(0, 0);
+    for (int m = i; m < r; ++m) v = v + conj(Xb[i * r + m]) * C[j * r + m];   // (Xb^H)_{im} C_{mj}
+    coef[(size_t)j * 2 * r + r + i] = mk<double>(-v.re, -v.im);
+  }
+  // off-diagonal part of C Lambda C^H
+  __shared__ double acc[256];
+  double s = 0.0;
+  for (int e = t; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    if (i == j) continue;
+    zd v = mk<double>(0, 0);
+    for (int m = 0; m < r; ++m) v = v + lam[m] * (C[m * r + i] * conj(C[m * r + j]));
+    s += norm2(v);
+  }
+  acc[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    double a = 0, l2 = 0;
+    for (int w = 0; w < (int)blockDim.x; ++w) a += acc[w];
+    for (int i = 0; i < r; ++i) l2 += lam[i] * lam[i];
+    out[0] = a;
+    out[1] = l2;
+  }
+}
+
+__global__ void dist_final_kernel(const zd *__restrict__ PP, int r, const double *__restrict__ lam, double *__restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double s = out[0];
+  for (int i = 0; i < r; ++i) s += 2.0 * lam[i] * lam[i] * PP[(size_t)i * r + i].re;
+  out[2] = sqrt(fmax(s, 0.0));
+  out[3] = sqrt(out[1]);
+}
+
+// ---------------------------------------------------------- Householder route
+// Compact-WY form Q = I - U T U^H of the r Householder reflectors that triangularise the
+// orthonormal factor V (Sec. 3.4, eq. Householder-mat), reconstructed from V itself: with
+// D = diag(d), d_i = -conj(V_ii)/|V_ii| (so no cancellation on the diagonal), the top block
+// B = I - V_top D has an unpivoted LU factorisation B = L_u R_u, and
+//   U = ([I; 0] - V D) R_u^{-1} (unit lower trapezoidal, U_top = L_u),  T = R_u L_u^{-H},
+// which gives Q[:, :r] = V D and Q^H V = [D^{-1}; 0].  The complement V^ is Q[:, r:].
+template <typename T>
+__global__ void top_block_kernel(const cx<T> *__restrict__ V, int r, zd *__restrict__ Vt) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int b = e / r, c = e % r;   // row b, column c of V (rows < r only)
+    const cx<T> v = V[(size_t)b * r + c];
+    Vt[(size_t)c * r + b] = mk<double>((double)v.re, (double)v.im);
+  }
+}
+
+// One CTA, r <= 32: D, L_u, R_u, R_u^{-1}, T and the coefficient -D R_u^{-1} of the U pass.
+__global__ void hh_setup_kernel(const zd *__restrict__ Vt, int r, zd *__restrict__ D, zd *__restrict__ Rinv,
+                                zd *__restrict__ T, zd *__restrict__ Cu, int *status) {
+  extern __shared__ zd sh[];
+  zd *B = sh, *Lu = sh + r * r, *Ru = sh + 2 * r * r, *Li = sh + 3 * r * r;   // Li = L_u^{-1}
+  const int t = threadIdx.x;
+  if (t < r) {
+    const zd v = Vt[(size_t)t * r + t];
+    const double a = sqrt(norm2(v));
+    D[t] = a > 0 ? mk<double>(-v.re / a, v.im / a) : mk<double>(-1, 0);
+  }
+  __syncthreads();
+  for (int e = t; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    B[e] = mk<double>(i == j ? 1.0 : 0.0, 0) - Vt[(size_t)j * r + i] * D[j];
+  }
+  __syncthreads();
+  if (t == 0) {
+    // Doolittle LU without pivoting: B = Lu Ru, Lu unit lower
+    bool bad = false;
+    for (int k = 0; k < r; ++k) {
+      for (int j = k; j < r; ++j) {
+        zd s = B[(size_t)j * r + k];
+        for (int m = 0; m < k; ++m) s = s - Lu[(size_t)m * r + k] * Ru[(size_t)j * r + m];
+        Ru[(size_t)j * r + k] = s;
+      }
+      const zd piv = Ru[(size_t)k * r + k];
+      const double pn = norm2(piv);
+      if (!(pn > 1e-300)) bad = true;
+      for (int i = 0; i < r; ++i) {
+        if (i < k) { Lu[(size_t)k * r + i] = mk<double>(0, 0); continue; }
+        if (i == k) { Lu[(size_t)k * r + i] = mk<double>(1, 0); continue; }
+        zd s = B[(size_t)k * r + i];
+        for (int m = 0; m < k; ++m) s = s - Lu[(size_t)m * r + i] * Ru[(size_t)k * r + m];
+        Lu[(size_t)k * r + i] = mk<double>((s.re * piv.re + s.im * piv.im) / pn, (s.im * piv.re - s.re * piv.im) / pn);
+      }
+      for (int i = k + 1; i < r; ++i) Ru[(size_t)k * r + i] = mk<double>(0, 0);
+    }
+    if (bad && status) atomicOr(status, ST_RANK);
+    // Rinv = Ru^{-1} (upper): column j by back substitution
+    for (int j = 0; j < r; ++j)
+      for (int i = r - 1; i >= 0; --i) {
+        zd s = mk<double>(i == j ? 1.0 : 0.0, 0);
+        for (int m = i + 1; m < r; ++m) s = s - Ru[(size_t)m * r + i] * Rinv[(size_t)j * r + m];
+        const zd d = Ru[(size_t)i * r + i];
+        const double dn = norm2(d);
+        Rinv[(size_t)j * r + i] = (i > j) ? mk<double>(0, 0)
+                                          : mk<double>((s.re * d.re + s.im * d.im) / dn, (s.im * d.re - s.re * d.im) / dn);
+      }
+    // Li = Lu^{-1} (unit lower): column j by forward substitution
+    for (int j = 0; j < r; ++j)
+      for (int i = 0; i < r; ++i) {
+        if (i < j) { Li[(size_t)j * r + i] = mk<double>(0, 0); continue; }
+        zd s = mk<double>(i == j ? 1.0 : 0.0, 0);
+        for (int m = j; m < i; ++m) s = s - Lu[(size_t)m * r + i] * Li[(size_t)j * r + m];
+        Li[(size_t)j * r + i] = s;
+      }
+  }
+  __syncthreads();
+  // T = Ru Lu^{-H} = Ru Li^H;  Cu = -D Rinv (row i of Rinv scaled by d_i)
+  for (int e = t; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    zd s = mk<double>(0, 0);
+    for (int m = 0; m < r; ++m) s = s + Ru[(size_t)m * r + i] * conj(Li[(size_t)m * r + j]);
+    T[e] = s;
+    Cu[e] = mk<double>(-1, 0) * (D[i] * Rinv[e]);
+  }
+}
+
+// U[0:r, :] += Rinv (rows of the N x r row-major block)
+template <typename T>
+__global__ void add_top_kernel(cx<T> *__restrict__ U, int r, const zd *__restrict__ Rinv) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int b = e / r, c = e % r;
+    const zd a = Rinv[(size_t)c * r + b];
+    U[(size_t)b * r + c] = U[(size_t)b * r + c] + mk<T>((T)a.re, (T)a.im);
+  }
+}
+
+__global__ void diag_conj_c_kernel(const double *__restrict__ lam, int r, double kappa, int model, zd *__restrict__ Dc,
+                                   const zd *__restrict__ K1, zd *__restrict__ Cq) {
+  // Dc = diag(conj c), Cq = -K1 diag(conj c)
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    const zd cc = conj(c_factor(lam[j], kappa, model));
+    Dc[e] = (i == j) ? cc : mk<double>(0, 0);
+    Cq[e] = mk<double>(-1, 0) * (K1[e] * cc);
+  }
+}
+
+__global__ void x11_from_g_kernel(const zd *__restrict__ G, int ldg, int r, const double *__restrict__ lam,
+                                  double kappa, int model, zd *__restrict__ X11, zd *__restrict__ Gh) {
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int i = e % r, j = e / r;
+    const zd a = G[(size_t)j * ldg + i], b = G[(size_t)i * ldg + j];
+    zd g = mk<double>(0.5 * (a.re + b.re), 0.5 * (a.im - b.im));
+    if (i == j) g.im = 0;
+    Gh[e] = g;
+    X11[e] = x11_factor(lam[i], lam[j], kappa, model) * g;
+  }
+}
+
 }  // namespace lrei
 
 using namespace lrei;
@@ -451,6 +648,8 @@ struct lrei_ctx {
   void *V = nullptr;
   void *blk[MAXB] = {};
   int nblk = 0;
+  void *Sbuf = nullptr;   // S = H Q_l of the current Krylov block (split mode)
+  bool fused_hv = false;
   // device workspace
   double *partial = nullptr;
   double *red = nullptr;
@@ -574,13 +773,20 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
   zd *red = reinterpret_cast<zd *>(c->red);
   for (int l = 0; l < s; ++l) {
     const int k = (l + 1) * r, ldr = (l + 2) * r;
-    // pass A: S = H Q_l, P = [Q_0..Q_l]^* S, S^*S
+    // pass A: S = H Q_l, P = [Q_0..Q_l]^* S, S^*S.  Split mode: S is formed once by the
+    // slab-major H.V kernel and both passes read it; fused mode recomputes H Q_l in each pass.
     TSArgs a{};
     a.nq = l + 1;
     a.gram_left = l + 1;
     for (int m = 0; m <= l; ++m) a.q[m] = qblock(c, m);
-    a.src = qblock(c, l);
-    a.apply_h = 1;
+    if (c->fused_hv) {
+      a.src = qblock(c, l);
+      a.apply_h = 1;
+    } else {
+      launch_hv(c->fp64, c->M, qblock(c, l), c->Sbuf, c->N, r, c->nsm, st);
+      a.src = c->Sbuf;
+      a.apply_h = 0;
+    }
     a.mode = 0;
     int rc = ts_pass(c, a);
     if (rc) return rc;
@@ -849,7 +1055,13 @@ int enqueue_ab_step(lrei_ctx *c, int m) {
   sm_zero(c->Rraw, KM, K, K, st);
   sm_set_identity(c->Rraw, KM, r, r, st);
   for (int i = 1; i < nb; ++i) {
-    int rc = (i == 1) ? orth_block(c, 1, c->V, 1, yk, qb, c->Rraw) : orth_block(c, i, raw[i], 0, nullptr, qb, c->Rraw);
+    int rc;
+    if (i == 1 && !c->fused_hv) {
+      launch_hv(c->fp64, c->M, c->V, yk, c->N, r, c->nsm, st);
+      rc = orth_block(c, 1, yk, 0, nullptr, qb, c->Rraw);
+    } else {
+      rc = (i == 1) ? orth_block(c, 1, c->V, 1, yk, qb, c->Rraw) : orth_block(c, i, raw[i], 0, nullptr, qb, c->Rraw);
+    }
     if (rc) return rc;
   }
   // coordinates of the raw blocks in the orthonormal frame Qbar = Q L^{-H}: Bbar = L^H Rraw
@@ -990,9 +1202,20 @@ int judge(lrei_ctx *c, double h, double *err) {
   int rc = ts_pass(c, a);
   if (rc) return rc;
   ::lrei::count_launch();
-  dist_kernel<<<1, 256, 5 * r * r * sizeof(zd), c->st>>>(reinterpret_cast<zd *>(c->red), r, c->Gbig, r, c->lam0_dev,
-                                                          c->dist_dev);
-  LREI_CUDA_TRY(cudaMemcpyAsync(c->host_small + 8, c->dist_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  dist_prep_kernel<<<1, 256, 6 * r * r * sizeof(zd), c->st>>>(reinterpret_cast<zd *>(c->red), r, c->Gbig, c->L, c->KM,
+                                                              c->lam0_dev, c->coefQ, c->dist_dev);
+  TSArgs p{};
+  p.nq = 2;
+  p.gram_left = 0;
+  p.q[0] = c->V;
+  p.q[1] = c->Vbig;
+  p.coefQ = c->coefQ;
+  p.mode = 2;
+  p.out = c->Sbuf;
+  if ((rc = ts_pass(c, p))) return rc;
+  ::lrei::count_launch();
+  dist_final_kernel<<<1, 32, 0, c->st>>>(reinterpret_cast<zd *>(c->red), r, c->lam0_dev, c->dist_dev);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->host_small + 8, c->dist_dev + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
   *err = (16.0 / 15.0) * c->host_small[8] / std::fmax(c->host_small[9], 1e-300);
   return LREI_OK;
@@ -1002,7 +1225,7 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
   int rc = build_graph(c, (int)LREI_RK4);
   if (rc) return rc;
   double h = c->ctrl_h > 0 ? c->ctrl_h : 1e-2;
-  int since_judge = c->ctrl_judge_every;   // judge the first step
+  int since_judge = c->ctrl_judge_every;   // the first step is judged
   bool last_rejected = false;
   int accepted_flag = 1;
   double f[3];
@@ -1015,6 +1238,7 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
     int sbits = read_feats(c, f);
     if (sbits & (ST_NONFINITE | ST_RANK)) return status_to_code(sbits);
     const double drift = f[2];
+    ++since_judge;
     const bool do_judge = since_judge >= c->ctrl_judge_every || last_rejected || c->ctrl_calib < 0 ||
                           (controller == 1 && c->learned_fallback > 0 && since_judge >= 2);
     double err;
@@ -1028,7 +1252,6 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       if (drift > 0) c->ctrl_calib = err / drift;
     } else {
       err = (c->ctrl_calib > 0 ? c->ctrl_calib : 1.0) * drift;
-      ++since_judge;
     }
     if (c->ctrl_record) {
       float x[NFEAT];
@@ -1152,11 +1375,21 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
   if (ts_init() || sm_init()) return fail(LREI_ERR_CUDA);
+  {
+    const int lim = 100 * 1024;
+    if (cudaFuncSetAttribute(hh_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+        cudaFuncSetAttribute(dist_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+        cudaFuncSetAttribute(dist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess ||
+        cudaFuncSetAttribute(obs_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+      return fail(LREI_ERR_CUDA);
+  }
   const size_t blk_bytes = (size_t)c->N * r_max * c->elem;
   c->nblk = 4;
   if ((rc = dalloc(c, &c->V, blk_bytes))) return fail(rc);
   for (int i = 0; i < c->nblk; ++i)
     if ((rc = dalloc(c, &c->blk[i], blk_bytes))) return fail(rc);
+  if ((rc = dalloc(c, &c->Sbuf, blk_bytes))) return fail(rc);
+  c->fused_hv = getenv("LREI_FUSED_HV") != nullptr;
   c->KM = 8 * r_max;   // RK_s needs (s+1) r <= 5 r, AB_m needs 2 m r <= 8 r
   const int KM = c->KM, R = r_max;
   const size_t zs = sizeof(zd);
@@ -1427,42 +1660,123 @@ int lrei_apply_h(lrei_ctx *c, const void *V_dev, void *Y_dev, int r) {
   return e == cudaSuccess ? LREI_OK : cuda_fail(e, "apply_h");
 }
 
-int lrei_rhs(lrei_ctx *c, void *Z_dev, void *W_dev, double *G_host, int complement) {
-  if (!c || !Z_dev || !W_dev) return LREI_ERR_ARG;
-  if (!c->has_state) return LREI_ERR_STATE;
-  if (complement != 0) return LREI_ERR_UNSUPPORTED;
+// Householder compact-WY factors of the current factor (U into U_dev, T and D to the host).
+static int householder_factors(lrei_ctx *c, void *U_dev) {
   const int r = c->r;
+  cudaStream_t st = c->st;
+  ::lrei::count_launch(2);
+  if (c->fp64) top_block_kernel<double><<<1, 256, 0, st>>>((const cx<double> *)c->V, r, c->Dm);
+  else top_block_kernel<float><<<1, 256, 0, st>>>((const cx<float> *)c->V, r, c->Dm);
+  hh_setup_kernel<<<1, 256, 4 * r * r * sizeof(zd), st>>>(c->Dm, r, c->X11, c->Ainv, c->L22, c->GR, c->status_dev);
+  // U = -V D Rinv (all rows), then U_top += Rinv
+  TSArgs u{};
+  u.nq = 1;
+  u.gram_left = 0;
+  u.q[0] = c->V;
+  u.coefQ = c->GR;
+  u.mode = 2;
+  u.out = U_dev;
+  int rc = ts_pass(c, u);
+  if (rc) return rc;
+  ::lrei::count_launch();
+  if (c->fp64) add_top_kernel<double><<<1, 256, 0, st>>>((cx<double> *)U_dev, r, c->Ainv);
+  else add_top_kernel<float><<<1, 256, 0, st>>>((cx<float> *)U_dev, r, c->Ainv);
+  return LREI_OK;
+}
+
+int lrei_rhs(lrei_ctx *c, void *Z_dev, void *W_dev, double *G_host, int complement) {
+  if (!c || !Z_dev || !W_dev || (complement != 0 && complement != 1)) return LREI_ERR_ARG;
+  if (!c->has_state) return LREI_ERR_STATE;
+  const int r = c->r;
+  if ((long long)r >= c->N && complement == 1) return LREI_ERR_ARG;
   enter(c);
-  // pass 1: Y = H V written to W, G = V^* Y
-  TSArgs a{};
-  a.nq = 1;
-  a.gram_left = 1;
-  a.q[0] = c->V;
-  a.src = c->V;
-  a.apply_h = 1;
-  a.mode = 0;
-  a.out = W_dev;
-  int rc = ts_pass(c, a);
-  if (rc) { leave(c); return rc; }
   zd *red = reinterpret_cast<zd *>(c->red);
-  sm_copy(red, 2 * r, r, r, c->G, r, c->st);
-  ::lrei::count_launch(); rhs_coef_kernel<<<1, 256, 0, c->st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->Dm, c->GR, c->X11);
-  // pass 2: W = Y diag(conj c) - V (G diag(conj c))   (in place over Y: row-local)
-  TSArgs b{};
-  b.nq = 1;
-  b.gram_left = 0;
-  b.q[0] = c->V;
-  b.src = W_dev;
-  b.apply_h = 0;
-  b.mode = 1;
-  b.coefS = c->Dm;
-  b.coefQ = c->GR;
-  b.out = W_dev;
-  if ((rc = ts_pass(c, b))) { leave(c); return rc; }
-  // pass 3: Z = V X11 + W
+  int rc = LREI_OK;
+  if (complement == 0) {
+    // pass 1: Y = H V written to W, G = V^* Y
+    TSArgs a{};
+    a.nq = 1;
+    a.gram_left = 1;
+    a.q[0] = c->V;
+    a.src = c->V;
+    a.apply_h = 1;
+    a.mode = 0;
+    a.out = W_dev;
+    if ((rc = ts_pass(c, a))) { leave(c); return rc; }
+    sm_copy(red, 2 * r, r, r, c->G, r, c->st);
+    ::lrei::count_launch();
+    rhs_coef_kernel<<<1, 256, 0, c->st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->Dm, c->GR, c->X11);
+    // pass 2: W = Y diag(conj c) - V (G diag(conj c))   (in place over Y: row-local)
+    TSArgs b{};
+    b.nq = 1;
+    b.gram_left = 0;
+    b.q[0] = c->V;
+    b.src = W_dev;
+    b.apply_h = 0;
+    b.mode = 1;
+    b.coefS = c->Dm;
+    b.coefQ = c->GR;
+    b.out = W_dev;
+    if ((rc = ts_pass(c, b))) { leave(c); return rc; }
+  } else {
+    // Householder route (Sec. 3.4-3.5): A = V^*H, A V^ = tail of A Q, X12 = diag(c) A V^,
+    // W = V^ X12^* = Q [0; X12^*], with Q = I - U T U^H.
+    void *U = c->blk[0], *Xh = c->blk[1];
+    if ((rc = householder_factors(c, U))) { leave(c); return rc; }
+    // P1: Y = H V (into W_dev), Grams [U, V]^* Y
+    TSArgs a{};
+    a.nq = 2;
+    a.gram_left = 2;
+    a.q[0] = U;
+    a.q[1] = c->V;
+    a.src = c->V;
+    a.apply_h = 1;
+    a.mode = 0;
+    a.out = W_dev;
+    if ((rc = ts_pass(c, a))) { leave(c); return rc; }
+    // G = V^*Y (rows r..2r-1 of the Gram), X11; K1 = T^H (U^*Y)
+    ::lrei::count_launch();
+    x11_from_g_kernel<<<1, 256, 0, c->st>>>(red + r, 3 * r, r, c->lam0_dev, c->kappa, c->model, c->X11, c->G);
+    sm_gemm('C', 'N', r, r, r, ONE, c->L22, r, red, 3 * r, ZERO, c->Bs, r, c->st);
+    ::lrei::count_launch();
+    diag_conj_c_kernel<<<1, 256, 0, c->st>>>(c->lam0_dev, r, c->kappa, c->model, c->Dm, c->Bs, c->coefQ);
+    // P2: Xh = (Y - U K1) diag(conj c), rows < r zero (= [0; X12^*]); Gram U^* Xh
+    TSArgs b{};
+    b.nq = 1;
+    b.gram_left = 1;
+    b.q[0] = U;
+    b.src = W_dev;
+    b.apply_h = 0;
+    b.mode = 1;
+    b.coefS = c->Dm;
+    b.coefQ = c->coefQ;
+    b.out = Xh;
+    b.zero_rows = r;
+    if ((rc = ts_pass(c, b))) { leave(c); return rc; }
+    // K2 = T (U^* Xh); P3: W = Xh - U K2
+    sm_gemm('N', 'N', r, r, r, MONE, c->L22, r, red, 2 * r, ZERO, c->Bs, r, c->st);
+    sm_set_identity(c->Lr, r, r, r, c->st);
+    TSArgs w3{};
+    w3.nq = 1;
+    w3.gram_left = 0;
+    w3.q[0] = U;
+    w3.src = Xh;
+    w3.apply_h = 0;
+    w3.mode = 1;
+    w3.coefS = c->Lr;
+    w3.coefQ = c->Bs;
+    w3.out = W_dev;
+    if ((rc = ts_pass(c, w3))) { leave(c); return rc; }
+  }
+  // Z = V X11 + W
   sm_set_identity(c->Ainv, r, r, r, c->st);
-  TSArgs z = b;
+  TSArgs z{};
+  z.nq = 1;
+  z.gram_left = 0;
+  z.q[0] = c->V;
   z.src = W_dev;
+  z.apply_h = 0;
+  z.mode = 1;
   z.coefS = c->Ainv;
   z.coefQ = c->X11;
   z.out = Z_dev;
@@ -1473,7 +1787,23 @@ int lrei_rhs(lrei_ctx *c, void *Z_dev, void *W_dev, double *G_host, int compleme
   }
   leave(c);
   LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
-  return LREI_OK;
+  const int s = read_status(c);
+  return status_to_code(s);
+}
+
+int lrei_householder(lrei_ctx *c, void *U_dev, double *T_host, double *D_host) {
+  if (!c || !U_dev) return LREI_ERR_ARG;
+  if (!c->has_state) return LREI_ERR_STATE;
+  const int r = c->r;
+  if ((long long)r >= c->N) return LREI_ERR_ARG;
+  enter(c);
+  int rc = householder_factors(c, U_dev);
+  if (rc) { leave(c); return rc; }
+  if (T_host) LREI_CUDA_TRY(cudaMemcpyAsync(T_host, c->L22, (size_t)r * r * sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+  if (D_host) LREI_CUDA_TRY(cudaMemcpyAsync(D_host, c->X11, (size_t)r * sizeof(zd), cudaMemcpyDeviceToHost, c->st));
+  leave(c);
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return status_to_code(read_status(c));
 }
 
 int lrei_last_status(lrei_ctx *c) { return c ? c->last_status : 0; }

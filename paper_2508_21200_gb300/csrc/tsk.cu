@@ -103,6 +103,87 @@ __global__ void __launch_bounds__(256) hv_kernel(const __grid_constant__ ModelAr
   }
 }
 
+// ------------------------------------------------ H.V, slab-major with shared-memory tiles
+// The N x r block is processed in column slabs of 32 bytes per row (4 complex64 or 2 complex128
+// columns), slab by slab (CTA index = slab * tiles + tile), so while one slab is being
+// processed its rows (N * 32 B: 32 MB at N = 2^20) stay resident in L2 and the bit-flip partner
+// rows of bonds that leave a tile are L2 hits.  A CTA stages a tile of TR = 2^t consecutive rows
+// of its slab in shared memory: bonds whose two bits are both below t find their partner in the
+// tile; the others read it from global memory (L2).
+template <typename T>
+__global__ void __launch_bounds__(256) hv2_kernel(const __grid_constant__ ModelArgs M, const cx<T> *__restrict__ X,
+                                                  cx<T> *__restrict__ Y, long long N, int r, int tbits) {
+  constexpr int SW = 32 / sizeof(cx<T>);   // complex elements per slab row
+  extern __shared__ __align__(16) unsigned char smem_hv[];
+  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_hv);   // TR x SW
+  const long long TR = 1LL << tbits;
+  const long long ntile = (N + TR - 1) / TR;
+  const int slab = (int)(blockIdx.x / ntile);
+  const long long t0 = (blockIdx.x % ntile) * TR;
+  const int c0 = slab * SW;
+  const int rows = (int)((N - t0) < TR ? (N - t0) : TR);
+  // stage the tile (16-byte vectors; SW * sizeof(cx<T>) = 32 bytes per row)
+  for (int e = threadIdx.x; e < rows * 2; e += blockDim.x) {
+    const int lr = e >> 1, half = e & 1;
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(X + (size_t)(t0 + lr) * r + c0) + half);
+    reinterpret_cast<float4 *>(tile + (size_t)lr * SW)[half] = v;
+  }
+  __syncthreads();
+  for (int lr = threadIdx.x; lr < rows; lr += blockDim.x) {
+    const uint32_t b = (uint32_t)(t0 + lr);
+    T diag = (T)(M.c0 + M.bz * (0.5 * M.n - (double)__popc(b)));
+    cx<T> acc[SW];
+#pragma unroll
+    for (int c = 0; c < SW; ++c) acc[c] = mk<T>(0, 0);
+    for (int k = 0; k < M.nb; ++k) {
+      if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
+        diag -= (T)M.jz[k];
+        const T j = (T)M.jxy[k];
+        const uint32_t pb = b ^ M.mask[k];
+        cx<T> v[SW];
+        if ((long long)M.mask[k] < TR) {
+          const cx<T> *p = tile + (size_t)(pb - (uint32_t)t0) * SW;
+#pragma unroll
+          for (int c = 0; c < SW; ++c) v[c] = p[c];
+        } else {
+          const float4 *p = reinterpret_cast<const float4 *>(X + (size_t)pb * r + c0);
+          float4 q0 = __ldg(p), q1 = __ldg(p + 1);
+          const cx<T> *qq0 = reinterpret_cast<const cx<T> *>(&q0);
+          const cx<T> *qq1 = reinterpret_cast<const cx<T> *>(&q1);
+#pragma unroll
+          for (int c = 0; c < SW / 2; ++c) { v[c] = qq0[c]; v[SW / 2 + c] = qq1[c]; }
+        }
+#pragma unroll
+        for (int c = 0; c < SW; ++c) {
+          acc[c].re = fma(j, v[c].re, acc[c].re);
+          acc[c].im = fma(j, v[c].im, acc[c].im);
+        }
+      }
+    }
+    const cx<T> *own = tile + (size_t)lr * SW;
+    cx<T> o[SW];
+#pragma unroll
+    for (int c = 0; c < SW; ++c) {
+      o[c].re = fma(diag, own[c].re, acc[c].re);
+      o[c].im = fma(diag, own[c].im, acc[c].im);
+    }
+    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)b * r + c0);
+    float w[2 * SW];
+#pragma unroll
+    for (int c = 0; c < SW; ++c) { w[2 * c] = (float)0; w[2 * c + 1] = (float)0; }
+    if (sizeof(T) == 4) {
+#pragma unroll
+      for (int c = 0; c < SW; ++c) { w[2 * c] = (float)o[c].re; w[2 * c + 1] = (float)o[c].im; }
+      dst[0] = make_float4(w[0], w[1], w[2], w[3]);
+      dst[1] = make_float4(w[4], w[5], w[6], w[7]);
+    } else {
+      double2 *dd = reinterpret_cast<double2 *>(dst);
+      dd[0] = make_double2((double)o[0].re, (double)o[0].im);
+      dd[1] = make_double2((double)o[SW - 1].re, (double)o[SW - 1].im);
+    }
+  }
+}
+
 // ------------------------------------------------------ accumulation
 // Error-free sum: s + e == a + b exactly (Knuth TwoSum).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
@@ -225,7 +306,7 @@ __global__ void __launch_bounds__(TS_THREADS) ts_kernel(const __grid_constant__ 
           const cx<T> *cm = cj + m * r;
           for (int i = 0; i < r; ++i) fma_(s, qrow[i], cm[i]);
         }
-        if (lr >= rows) s = mk<T>(0, 0);
+        if (lr >= rows || row0 + lr < a.zero_rows) s = mk<T>(0, 0);
         ns[e] = s;
         if (lr < rows && out) out[(size_t)(row0 + lr) * r + j] = s;
       }
@@ -264,18 +345,30 @@ __global__ void __launch_bounds__(TS_THREADS) ts_kernel(const __grid_constant__ 
 template <typename T> struct TS2 {
   static constexpr int MI = sizeof(T) == 4 ? 4 : 2;
   static constexpr int MJ = 4;
-  static constexpr int PAD = sizeof(T) == 4 ? 2 : 1;
-  static constexpr int FLUSH = sizeof(T) == 4 ? 4 : 1 << 30;
+  static constexpr int PAD = sizeof(T) == 4 ? 2 : 1;     // row padding (complex elements)
+  static constexpr int STAG = sizeof(T) == 4 ? 8 : 4;    // block base stagger (64 bytes)
+  static constexpr int FLUSH = sizeof(T) == 4 ? 2 : 1 << 30;
 };
 
 __host__ __device__ inline int ts2_rp(int r) { return (r + 3) & ~3; }
 
+// Gram work split: NMT micro-tiles, nph (power of two) phases per micro-tile; the phases of one
+// micro-tile are consecutive lanes of one warp, so their partials are combined by shuffles.
+__host__ __device__ inline int ts2_nph(int nmt) {
+  int p = 1;
+  while (p < 16 && nmt * p * 2 <= TS_THREADS) p *= 2;
+  return p;
+}
+
 template <typename T>
 __host__ __device__ inline size_t ts2_bytes(int nq, int gl, int r, int tr, int mode, int mt) {
   const int rp = ts2_rp(r), RS = rp + TS2<T>::PAD;
-  size_t b = ((size_t)nq * tr * RS + 2 * (size_t)tr * RS) * sizeof(cx<T>);
+  const size_t bstride = (size_t)tr * RS + TS2<T>::STAG;
+  size_t b = ((size_t)(nq + 2) * bstride) * sizeof(cx<T>);
   if (mode != 0) b += (size_t)(nq + 1) * rp * rp * sizeof(cx<T>);
-  b += (size_t)TS_THREADS * mt * TS2<T>::MI * TS2<T>::MJ * 16;   // per-thread accumulators
+  const int nmt = (gl + 1) * rp / TS2<T>::MI * (rp / TS2<T>::MJ);
+  b += (size_t)nmt * TS2<T>::MI * TS2<T>::MJ * 16;   // one accumulator set per micro-tile
+  (void)mt;
   return b;
 }
 
@@ -287,27 +380,29 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
   extern __shared__ __align__(16) unsigned char smem[];
   const int r = a.r, nq = a.nq, gl = a.gram_left;
   const int rp = ts2_rp(r), RS = rp + TS2<T>::PAD;
-  const int tid = threadIdx.x;
+  const size_t BS = (size_t)tr * RS + TS2<T>::STAG;     // staggered block stride
+  const int tid = threadIdx.x, lane = tid & 31;
   cx<T> *qs = reinterpret_cast<cx<T> *>(smem);
-  cx<T> *gs = qs + (size_t)nq * tr * RS;
-  cx<T> *ns = gs + (size_t)tr * RS;
-  cx<T> *cs = ns + (size_t)tr * RS;
+  cx<T> *gs = qs + (size_t)nq * BS;
+  cx<T> *ns = gs + BS;
+  cx<T> *cs = ns + BS;
   const int ncoef = (a.mode != 0) ? (nq + 1) * rp * rp : 0;
-  double *slots = reinterpret_cast<double *>(cs + ncoef);   // [TS_THREADS][MT][MI*MJ] x 16 bytes
+  double *slots = reinterpret_cast<double *>(cs + ncoef);   // [NMT][MI*MJ] x 16 bytes
 
-  for (int e = tid; e < ncoef; e += TS_THREADS) cs[e] = coefg[e];
-  for (int e = tid; e < TS_THREADS * MT * MI * MJ * 2; e += TS_THREADS) slots[e] = 0.0;
-
-  // Gram micro-tile assignment
   const int nI = (gl + 1) * rp / MI, nJ = rp / MJ, NMT = nI * nJ;
-  const int nph = (MT == 1 && NMT < TS_THREADS) ? TS_THREADS / NMT : 1;
-  const int ph = (MT == 1) ? tid / NMT : 0;
+  for (int e = tid; e < ncoef; e += TS_THREADS) cs[e] = coefg[e];
+  for (int e = tid; e < NMT * MI * MJ * 2; e += TS_THREADS) slots[e] = 0.0;
+
+  // Gram micro-tile assignment: MT == 1 -> micro-tile tid / nph, phase tid % nph (lanes);
+  // MT == 2 -> micro-tiles tid and tid + 256, one phase.
+  const int nph = (MT == 1) ? ts2_nph(NMT) : 1;
+  const int ph = (MT == 1) ? (tid % nph) : 0;
   int mts[MT];
   bool mval[MT];
 #pragma unroll
   for (int u = 0; u < MT; ++u) {
-    mts[u] = (MT == 1) ? tid % NMT : tid + u * TS_THREADS;
-    mval[u] = (MT == 1) ? (ph < nph) : (mts[u] < NMT);
+    mts[u] = (MT == 1) ? tid / nph : tid + u * TS_THREADS;
+    mval[u] = mts[u] < NMT;
   }
   cx<T> acc[MT][MI][MJ];
 #pragma unroll
@@ -317,6 +412,23 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
 #pragma unroll
       for (int y = 0; y < MJ; ++y) acc[u][x][y] = mk<T>(0, 0);
   __syncthreads();
+
+  auto flush = [&]() {
+#pragma unroll
+    for (int u = 0; u < MT; ++u)
+#pragma unroll
+      for (int x = 0; x < MI; ++x)
+#pragma unroll
+        for (int y = 0; y < MJ; ++y) {
+          cx<T> v = acc[u][x][y];
+          for (int o = nph >> 1; o > 0; o >>= 1) {   // combine the phases of this micro-tile
+            v.re += __shfl_down_sync(0xffffffffu, v.re, o, nph);
+            v.im += __shfl_down_sync(0xffffffffu, v.im, o, nph);
+          }
+          if (ph == 0 && mval[u]) Acc<T>::add(slots, mts[u] * MI * MJ + x * MJ + y, v);
+          acc[u][x][y] = mk<T>(0, 0);
+        }
+  };
 
   const long long ntiles = (a.N + tr - 1) / tr;
   const int gpr = r / CPT;
@@ -346,10 +458,23 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
     // Q tiles (rows of one block are contiguous in global memory)
     for (int m = 0; m < nq; ++m) {
       const cx<T> *qm = reinterpret_cast<const cx<T> *>(a.q[m]) + (size_t)row0 * r;
-      cx<T> *dst = qs + (size_t)m * tr * RS;
-      for (int e = tid; e < tr * rp; e += TS_THREADS) {
-        const int lr = e / rp, c = e % rp;
-        dst[lr * RS + c] = (lr < rows && c < r) ? ldg1(qm + (size_t)lr * r + c) : mk<T>(0, 0);
+      cx<T> *dst = qs + (size_t)m * BS;
+      if (rp == r && (r % 2 == 0) && sizeof(T) == 4) {
+        // 16-byte vectors: two complex64 per load
+        const int hr = r / 2;
+        for (int e = tid; e < tr * hr; e += TS_THREADS) {
+          const int lr = e / hr, c = (e % hr) * 2;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (lr < rows) v = __ldg(reinterpret_cast<const float4 *>(qm + (size_t)lr * r + c));
+          cx<T> *d = dst + lr * RS + c;
+          d[0] = mk<T>((T)v.x, (T)v.y);
+          d[1] = mk<T>((T)v.z, (T)v.w);
+        }
+      } else {
+        for (int e = tid; e < tr * rp; e += TS_THREADS) {
+          const int lr = e / rp, c = e % rp;
+          dst[lr * RS + c] = (lr < rows && c < r) ? ldg1(qm + (size_t)lr * r + c) : mk<T>(0, 0);
+        }
       }
     }
     __syncthreads();
@@ -364,7 +489,7 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
         for (int y = 0; y < 4; ++y) o[y] = mk<T>(0, 0);
         const int mlast = (a.mode == 1) ? nq : nq - 1;
         for (int m = 0; m <= mlast; ++m) {
-          const cx<T> *X = (m < nq) ? qs + (size_t)m * tr * RS + lr * RS : gs + lr * RS;
+          const cx<T> *X = (m < nq) ? qs + (size_t)m * BS + lr * RS : gs + lr * RS;
           const cx<T> *C = cs + (size_t)m * rp * rp + j0;
           for (int i = 0; i < r; ++i) {
             const cx<T> x = X[i];
@@ -376,7 +501,7 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
           const int j = j0 + y;
-          const cx<T> v = (lr < rows && j < r) ? o[y] : mk<T>(0, 0);
+          const cx<T> v = (lr < rows && j < r && row0 + lr >= a.zero_rows) ? o[y] : mk<T>(0, 0);
           ns[lr * RS + j] = v;
           if (lr < rows && j < r && out) out[(size_t)(row0 + lr) * r + j] = v;
         }
@@ -393,7 +518,7 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
       if (!mval[u]) continue;
       const int I = mts[u] / nJ, J = mts[u] % nJ;
       const int i0 = I * MI, m = i0 / rp, ii0 = i0 % rp, j0 = J * MJ;
-      const cx<T> *L = (m < gl) ? qs + (size_t)m * tr * RS : G;
+      const cx<T> *L = (m < gl) ? qs + (size_t)m * BS : G;
       for (int lr = ph; lr < tr; lr += nph) {
         cx<T> lv[MI], gv[MJ];
 #pragma unroll
@@ -408,43 +533,24 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
     }
     if (++since_flush >= TS2<T>::FLUSH) {
       since_flush = 0;
-#pragma unroll
-      for (int u = 0; u < MT; ++u)
-#pragma unroll
-        for (int x = 0; x < MI; ++x)
-#pragma unroll
-          for (int y = 0; y < MJ; ++y) {
-            Acc<T>::add(slots, (tid * MT + u) * MI * MJ + x * MJ + y, acc[u][x][y]);
-            acc[u][x][y] = mk<T>(0, 0);
-          }
+      flush();
     }
     __syncthreads();
   }
-#pragma unroll
-  for (int u = 0; u < MT; ++u)
-#pragma unroll
-    for (int x = 0; x < MI; ++x)
-#pragma unroll
-      for (int y = 0; y < MJ; ++y) Acc<T>::add(slots, (tid * MT + u) * MI * MJ + x * MJ + y, acc[u][x][y]);
+  flush();
   __syncthreads();
-  // reduce over phases and write the CTA partial in the column-major ((gl+1) r) x r layout
+  // write the CTA partial in the column-major ((gl+1) r) x r layout
   const int ldg_ = (gl + 1) * r, nent = ldg_ * r;
   double *outp = a.partial + (size_t)blockIdx.x * nent * 2;
   for (int e = tid; e < nent; e += TS_THREADS) {
     const int j = e / ldg_, row = e % ldg_, m = row / r, i = row % r;
-    const int ic = m * rp + i;                          // row in the padded concatenation
+    const int ic = m * rp + i;
     const int I = ic / MI, x = ic % MI, J = j / MJ, y = j % MJ;
-    const int mt = I * nJ + J;
-    cx<double> sum = mk<double>(0, 0);
-    if (MT == 1) {
-      for (int p = 0; p < nph; ++p) sum = sum + Acc<T>::get(slots, (p * NMT + mt) * MI * MJ + x * MJ + y);
-    } else {
-      const int owner = mt % TS_THREADS, u = mt / TS_THREADS;
-      sum = Acc<T>::get(slots, (owner * MT + u) * MI * MJ + x * MJ + y);
-    }
+    const cx<double> sum = Acc<T>::get(slots, (I * nJ + J) * MI * MJ + x * MJ + y);
     outp[2 * e] = sum.re;
     outp[2 * e + 1] = sum.im;
   }
+  (void)lane;
 }
 
 // Coefficients in the padded row-major layout of ts2_kernel: row m*rp + i, column j.
@@ -610,6 +716,18 @@ void launch_reduce(const double *partial, int nparts, int len_doubles, double *o
 }
 
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st) {
+  const int sw = fp64 ? 2 : 4;
+  if (r % sw == 0 && !g_force_v1) {
+    int tbits = M.n < 11 ? M.n : 11;
+    const long long TR = 1LL << tbits;
+    const long long ntile = (N + TR - 1) / TR;
+    const int grid = (int)(ntile * (r / sw));
+    const size_t bytes = (size_t)TR * 32;
+    ::lrei::count_launch();
+    if (fp64) hv2_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
+    else hv2_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
+    return;
+  }
   auto grid_for = [&](int cpt) {
     long long total = N * (r / cpt);
     long long g = (total + 255) / 256;
@@ -780,6 +898,8 @@ int ts_init() {
   set((const void *)ts2_kernel<float, 4, 2>);
   set((const void *)ts2_kernel<float, 2, 2>);
   set((const void *)ts2_kernel<float, 1, 2>);
+  set((const void *)hv2_kernel<double>);
+  set((const void *)hv2_kernel<float>);
   set((const void *)obs_kernel<double>);
   set((const void *)obs_kernel<float>);
   return e == cudaSuccess ? 0 : -1;

@@ -27,6 +27,7 @@ struct TSArgs {
   double *partial;
   int mode;
   void *coef_scratch;   // device, >= (MAXB+1)*MAX_R*MAX_R*16 bytes (converted coefficients)
+  long long zero_rows;  // modes 1, 2: rows < zero_rows of the new block are set to zero
 };
 
 // Returns the grid size used (number of partials written), or -1 on error.
