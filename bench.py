@@ -252,11 +252,12 @@ def run_ours(args):
     # first on plain-controller data from small chains (GPU kernels), then the n=20 workload is
     # integrated adaptively over the same simulated time as K fixed steps of dt
     learned = None
+    learned_error = None
     if not args.no_learned:
         from paper_2508_21200_gb300 import controller as ctl
         train_w = [li.workload(4, t, n=n, r=8, kappa=0.1) for t, n in ((1, 10), (2, 11), (3, 12))]
         t_tr = time.perf_counter()
-        Xtr, Ytr = ctl.generate(train_w, t_end=0.3, tols=(1e-6, 1e-7), precision="mixed")
+        Xtr, Ytr = ctl.generate(train_w, t_end=0.3, tols=(1e-5, 1e-6), precision="mixed")
         net, tr_loss = ctl.fit(Xtr, Ytr, iters=2000, lr=2e-3)
         t_tr = time.perf_counter() - t_tr
         Ll = make("mixed")
@@ -268,7 +269,10 @@ def run_ours(args):
         _barrier(world)
         l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0.record(stream)
-        Ll.step_adaptive((W + K) * w.dt, args.tol, 1)
+        try:
+            Ll.step_adaptive((W + K) * w.dt, args.tol, 1)
+        except Exception as e:   # reported, and the headline falls back to the fixed-dt line
+            learned_error = f"{type(e).__name__}: {e}"
         l1.record(stream)
         torch.cuda.synchronize()
         launches_l = Ll.kernel_launches()
@@ -281,6 +285,8 @@ def run_ours(args):
                    "controller_stats": stl, "obs_rel_err_vs_fp64_fixed_dt": err_l, "gpu_launches": launches_l,
                    "train_rows": int(Xtr.shape[0]), "train_loss": tr_loss, "train_seconds": round(t_tr, 1)}
         del Ll, net
+        if learned_error is not None:
+            learned = None
 
     # ---- roofline: matrix-free H.V (complex64), timed alone with events on its stream
     N, r = 1 << w.n, w.r
@@ -342,7 +348,7 @@ def run_ours(args):
            "mixed_fixed_dt": {"steps_per_s": round(value, 3), "ms_per_step": round(ms_max, 4)},
            "fp64_gpu": {"steps_per_s": round(1000.0 / ms_fp64, 3), "ms_per_step": round(ms_fp64, 3), "steps_timed": Kd},
            "speedup_vs_fp64": round((head / (1000.0 / ms_fp64)), 2),
-           "learned": learned,
+           "learned": learned if learned_error is None else {"error": learned_error},
            "obs_rel_err_vs_fp64": err, "ritz_rel_err_vs_fp64": err_mu,
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
     if cpu is not None:
@@ -400,7 +406,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--judge-every", type=int, default=8)
     ap.add_argument("--cpu-sample", type=int, default=0)
     args = ap.parse_args()

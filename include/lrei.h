@@ -44,7 +44,8 @@ typedef enum {
   LREI_ERR_OOM = -7,         /* device allocation failed */
   LREI_ERR_CUDA = -8,        /* other CUDA runtime error */
   LREI_ERR_STATE = -9,       /* call out of order (e.g. step before set_state) */
-  LREI_ERR_TIMEOUT = -10     /* a bounded device-side wait ran out */
+  LREI_ERR_TIMEOUT = -10,    /* a bounded device-side wait ran out */
+  LREI_ERR_STEP = -11        /* adaptive step size fell below its floor (tolerance not reachable) */
 } lrei_status;
 
 typedef enum { LREI_QLL = 0, LREI_QLLG = 1 } lrei_model;
@@ -122,7 +123,14 @@ int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
 /* Advance to t_end with RK4 and an adaptive step: controller 0 = the plain
  * rule (spectral-drift estimate, step doubling as judge), 1 = the learned
  * controller (falls back to the plain rule when its prediction is judged
- * wrong).  tol bounds the relative local error per step. */
+ * wrong).  tol bounds the relative local error per step; it is raised to the
+ * rounding floor of the context's precision (LREI_TOL_FLOOR_FP64,
+ * LREI_TOL_FLOOR_MIXED), below which the step-doubling estimate is noise.
+ * Returns LREI_ERR_STEP, with the state of the last accepted step kept, when
+ * the step size falls below 1e-12 * max(1, |t_end|) or 64 steps in a row
+ * are rejected. */
+#define LREI_TOL_FLOOR_FP64 1e-13
+#define LREI_TOL_FLOOR_MIXED 5e-6
 int lrei_step_adaptive(lrei_ctx *ctx, double t_end, double tol, int controller);
 
 /* Compute observables of the current state into a host struct (syncs). */
@@ -162,6 +170,10 @@ int lrei_householder(lrei_ctx *ctx, void *U_dev, double *T_host, double *D_host)
  * 1 non-finite, 2 small eigensolver sweep limit, 4 rank-deficient factor,
  * 8 bounded wait ran out, 16 trace, 32 eigenpair residual above tolerance. */
 int lrei_last_status(lrei_ctx *ctx);
+
+/* Cumulative small-eigensolver counters of this process on the current device
+ * (diagnostics): FP32 Jacobi calls, their sweeps, FP64 Jacobi calls, their sweeps. Syncs. */
+int lrei_debug_counters(unsigned long long *out4);
 
 /* Number of kernels this library launched on the context's stream since the
  * last call (resets the counter). */

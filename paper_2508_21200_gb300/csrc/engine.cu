@@ -26,6 +26,7 @@
 #include "small.cuh"
 #include "tsk.cuh"
 
+namespace lrei { int sm_read_counters(unsigned long long *out); }
 // controller network inference on a given stream (mlp.cu)
 int lrei_mlp_forward_on(lrei_mlp *net, const float *X, int B, float *Y, cudaStream_t st);
 
@@ -1225,6 +1226,10 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
   int rc = build_graph(c, (int)LREI_RK4);
   if (rc) return rc;
   double h = c->ctrl_h > 0 ? c->ctrl_h : 1e-2;
+  // below the rounding floor of the stored factor the judged error is noise: never ask for less
+  tol = std::fmax(tol, c->fp64 ? LREI_TOL_FLOOR_FP64 : LREI_TOL_FLOOR_MIXED);
+  const double h_min = 1e-12 * std::fmax(1.0, std::fabs(t_end));
+  int rejected_in_row = 0;
   int since_judge = c->ctrl_judge_every;   // the first step is judged
   bool last_rejected = false;
   int accepted_flag = 1;
@@ -1269,10 +1274,15 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       last_rejected = true;
       accepted_flag = 0;
       if (controller == 1 && do_judge) c->learned_fallback = 16;
+      if (++rejected_in_row >= 64 || h < h_min) {
+        c->ctrl_h = h;
+        return LREI_ERR_STEP;
+      }
       continue;
     }
     c->t += hs;
     c->st_accepted += 1;
+    rejected_in_row = 0;
     last_rejected = false;
     accepted_flag = 1;
     double ratio = std::fmin(5.0, std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2)));
@@ -1290,6 +1300,10 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
     }
     if (c->learned_fallback > 0) --c->learned_fallback;
     h = hs * ratio;
+    if (h < h_min) {
+      c->ctrl_h = h;
+      return LREI_ERR_STEP;
+    }
   }
   c->ctrl_h = h;
   return LREI_OK;
@@ -1312,6 +1326,7 @@ const char *lrei_error_string(int code) {
     case LREI_ERR_CUDA: return "CUDA runtime error";
     case LREI_ERR_STATE: return "call out of order";
     case LREI_ERR_TIMEOUT: return "bounded device wait ran out";
+    case LREI_ERR_STEP: return "adaptive step size underflow";
     default: return "unknown error";
   }
 }
@@ -1807,6 +1822,12 @@ int lrei_householder(lrei_ctx *c, void *U_dev, double *T_host, double *D_host) {
 }
 
 int lrei_last_status(lrei_ctx *c) { return c ? c->last_status : 0; }
+
+int lrei_debug_counters(unsigned long long *out4) {
+  if (!out4) return LREI_ERR_ARG;
+  cudaDeviceSynchronize();
+  return sm_read_counters(out4) == 0 ? LREI_OK : LREI_ERR_CUDA;
+}
 
 long long lrei_kernel_launches(lrei_ctx *c) {
   if (!c) return 0;

@@ -11,6 +11,9 @@
 
 namespace lrei {
 
+// [0] FP32 Jacobi calls, [1] FP32 sweeps, [2] FP64 Jacobi calls, [3] FP64 sweeps (diagnostics)
+__device__ unsigned long long g_jacobi_counters[4];
+
 __device__ __forceinline__ zd zdiv_real(zd a, double d) { return mk<double>(a.re / d, a.im / d); }
 __device__ __forceinline__ zd zdiv(zd a, zd d) {
   const double n = d.re * d.re + d.im * d.im;
@@ -305,34 +308,38 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const zd *__restrict__ Ain,
         rot[pi] = R;
       }
       __syncthreads();
-      // A <- A J and U <- U J (columns p, q), J = [[c, s], [-conj(s), c]]
-      for (int e = t; e < np * kp; e += nt) {
-        const Rot<T> R = rot[e / kp];
-        const int i = e % kp;
-        if (R.s.re == 0 && R.s.im == 0) continue;
-        cx<T> *cp = A + (size_t)R.p * kp, *cq = A + (size_t)R.q * kp;
-        const cx<T> x = cp[i], y = cq[i];
-        cp[i] = R.c * x - conj(R.s) * y;
-        cq[i] = R.s * x + R.c * y;
-        cx<T> *up = U + (size_t)R.p * kp, *uq = U + (size_t)R.q * kp;
-        const cx<T> ux = up[i], uy = uq[i];
-        up[i] = R.c * ux - conj(R.s) * uy;
-        uq[i] = R.s * ux + R.c * uy;
-      }
-      __syncthreads();
-      // A <- J^H A (rows p, q)
-      for (int e = t; e < np * kp; e += nt) {
-        const Rot<T> R = rot[e / kp];
-        const int i = e % kp;
-        if (R.s.re == 0 && R.s.im == 0) continue;
-        const cx<T> x = A[(size_t)i * kp + R.p], y = A[(size_t)i * kp + R.q];
-        A[(size_t)i * kp + R.p] = R.c * x - R.s * y;
-        A[(size_t)i * kp + R.q] = conj(R.s) * x + R.c * y;
+      // A <- J^H A J on 2x2 blocks (pairs a, b): every element is read and written once;
+      // U <- U J on the pairs' columns.  J = [[c, s], [-conj(s), c]] on (p, q).
+      for (int e = t; e < np * np + np * kp; e += nt) {
+        if (e < np * np) {
+          const Rot<T> Ra = rot[e % np], Rb = rot[e / np];
+          cx<T> *a0 = A + (size_t)Rb.p * kp, *a1 = A + (size_t)Rb.q * kp;
+          const cx<T> x00 = a0[Ra.p], x10 = a0[Ra.q], x01 = a1[Ra.p], x11 = a1[Ra.q];
+          // Y = X J_b
+          const cx<T> y00 = Rb.c * x00 - conj(Rb.s) * x01, y01 = Rb.s * x00 + Rb.c * x01;
+          const cx<T> y10 = Rb.c * x10 - conj(Rb.s) * x11, y11 = Rb.s * x10 + Rb.c * x11;
+          // X' = J_a^H Y
+          a0[Ra.p] = Ra.c * y00 - Ra.s * y10;
+          a1[Ra.p] = Ra.c * y01 - Ra.s * y11;
+          a0[Ra.q] = conj(Ra.s) * y00 + Ra.c * y10;
+          a1[Ra.q] = conj(Ra.s) * y01 + Ra.c * y11;
+        } else {
+          const int f = e - np * np;
+          const Rot<T> R = rot[f / kp];
+          const int i = f % kp;
+          if (R.s.re == 0 && R.s.im == 0) continue;
+          cx<T> *up = U + (size_t)R.p * kp, *uq = U + (size_t)R.q * kp;
+          const cx<T> ux = up[i], uy = uq[i];
+          up[i] = R.c * ux - conj(R.s) * uy;
+          uq[i] = R.s * ux + R.c * uy;
+        }
       }
       __syncthreads();
     }
     if (sweep == max_sweeps - 1 && t == 0 && status) atomicOr(status, ST_EIG_NOCONV);
+    if (t == 0) atomicAdd(&g_jacobi_counters[sizeof(T) == 4 ? 1 : 3], 1ull);
   }
+  if (t == 0) atomicAdd(&g_jacobi_counters[sizeof(T) == 4 ? 0 : 2], 1ull);
   // sort eigenvalues decreasing (ties by index) and write out
   for (int i = t; i < k; i += nt) {
     const T wi = A[(size_t)i * kp + i].re;
@@ -560,5 +567,11 @@ int sm_init() {
   cudaError_t a = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t b = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return (a == cudaSuccess && b == cudaSuccess) ? 0 : -1;
+}
+}  // namespace lrei
+
+namespace lrei {
+int sm_read_counters(unsigned long long *out) {
+  return cudaMemcpyFromSymbol(out, g_jacobi_counters, sizeof(unsigned long long) * 4) == cudaSuccess ? 0 : -1;
 }
 }  // namespace lrei

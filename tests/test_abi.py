@@ -45,6 +45,13 @@ def test_error_strings_without_gpu(lib_path):
     lib.lrei_error_string.restype = ctypes.c_char_p
     assert lib.lrei_error_string(0) == b"ok"
     assert b"argument" in lib.lrei_error_string(-1)
+    # every status the header declares has its own message
+    hdr = open(os.path.join(ROOT, "include", "lrei.h")).read()
+    codes = [int(v) for v in re.findall(r"LREI_(?:OK|ERR_\w+) = (-?\d+)", hdr)]
+    assert len(codes) >= 12 and 0 in codes
+    msgs = [lib.lrei_error_string(c) for c in codes]
+    assert len(set(msgs)) == len(codes) and b"unknown error" not in msgs
+    assert lib.lrei_error_string(-99) == b"unknown error"
 
 
 def test_create_rejects_bad_arguments_before_touching_the_gpu(lib_path):

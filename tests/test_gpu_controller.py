@@ -67,6 +67,21 @@ def test_learned_controller_with_untrained_network_stays_safe():
     assert _err(o, ref) < 1e-7
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tolerance_below_rounding_floor_terminates(precision):
+    # a tolerance below what the stored factor can resolve is raised to the precision's floor
+    # (1e-13 FP64, 5e-6 complex64) instead of shrinking the step without end
+    w = li.workload(1, n=7, r=3)
+    L = Lrei(w.n, w.bonds, w.B, w.kappa, w.model, precision, w.r)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    L.set_state(torch.from_numpy(w.V).to("cuda", dt), w.lam)
+    L.controller_config(judge_every=1, record=False, h0=0.01)
+    L.step_adaptive(0.05, 1e-16, 0)
+    st = L.controller_stats()
+    assert abs(L.observables()["t"] - 0.05) < 1e-12
+    assert st["accepted"] >= 1 and st["rejected"] < 64
+
+
 def test_records_have_features_and_judged_errors():
     w = li.workload(1, n=7, r=3)
     L = Lrei(w.n, w.bonds, w.B, w.kappa, w.model, "fp64", w.r)
@@ -88,7 +103,7 @@ def test_trained_network_gain_over_plain_rule():
     train_w = [li.workload(4, t, n=n, r=4, kappa=0.1) for t, n in ((1, 9), (2, 10), (3, 11))]
     X, Y = ctl.generate(train_w, t_end=0.3, tols=(1e-7, 1e-9))
     net, loss = ctl.fit(X, Y, iters=2000, lr=2e-3)
-    assert loss < 0.5 * float(np.var(Y)) + 1e-6
+    assert loss < 0.35 * float(np.var(Y)) + 1e-6     # R^2 > 0.3 (loss = half the mean square)
     w = li.workload(4, 9, n=10, r=4, kappa=0.1)
     t_end, tol = 0.4, 1e-8
     ref = _reference(w, t_end)
