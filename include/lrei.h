@@ -179,6 +179,28 @@ int lrei_debug_counters(unsigned long long *out4);
  * last call (resets the counter). */
 long long lrei_kernel_launches(lrei_ctx *ctx);
 
+/* ---- observables without device allocation ---------------------------- */
+/* For callers that cannot allocate device memory: hosts whose own allocator has reserved
+ * all of it (a framework's caching pool, a fixed memory budget) and monitoring loops that
+ * must not pay an allocation's latency or fragment the heap on every call.  Computes
+ * the observables of rho = V diag(Lambda) V^* exactly as lrei_observables does for a
+ * context holding the same factor, but without a context: n, J and B describe the
+ * Hamiltonian as in lrei_create, V_dev is the N x r factor (row-major, ld = r, dtype
+ * LREI_C128 or LREI_C64), Lambda_host its r weights.  ritz and t are left zero.
+ * The paper has no counterpart: this is a deployment variant of the observable pass.
+ * Scratch memory is one static device array of about 3.8 MB inside this library, held
+ * by every GPU that loads it until the process exits; nothing is allocated per call.
+ * The first call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  Every part of the array a
+ * call reads is first written by that call, so no part of it has to start at zero.  All
+ * calls share the array:
+ * calls that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  r > LREI_NOALLOC_MAX_R returns LREI_ERR_ARG.  Syncs the
+ * stream. */
+#define LREI_NOALLOC_MAX_R 16
+int lrei_observables_noalloc(int n, const lrei_bonds *J, const double B[3], const void *V_dev, int r,
+                             int dtype, const double *Lambda_host, void *cuda_stream, lrei_obs *out);
+
 /* ---- step/rank controller network ------------------------------------- */
 /* A three-layer FP32 perceptron y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3,
  * hidden width 128, trained on the GPU by its own backward and Adam kernels.

@@ -628,6 +628,11 @@ __global__ void x11_from_g_kernel(const zd *__restrict__ G, int ldg, int r, cons
   }
 }
 
+void launch_obs_final(const double *red, int r, const double *lam, double *out, cudaStream_t st) {
+  ::lrei::count_launch();
+  obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), st>>>(red, r, lam, out);
+}
+
 }  // namespace lrei
 
 using namespace lrei;

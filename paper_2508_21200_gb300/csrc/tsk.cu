@@ -828,6 +828,26 @@ int launch_obs(bool fp64, const ModelArgs &M, const void *V, long long N, int r,
   return grid;
 }
 
+
+// Same pass with the number of partial sums capped (used by the allocation-free observables).
+int launch_obs_capped(bool fp64, const ModelArgs &M, const void *V, long long N, int r, double *partial,
+                      int max_grid, cudaStream_t st) {
+  const int tr = 16;
+  const long long ntiles = (N + tr - 1) / tr;
+  int grid = (int)(ntiles < (long long)max_grid ? ntiles : max_grid);
+  if (grid < 1) grid = 1;
+  const size_t nent = (size_t)OBS_BLOCKS * r * r;
+  if (fp64) {
+    size_t bytes = 5 * (size_t)tr * r * sizeof(cx<double>) + nent * 16;
+    ::lrei::count_launch(); obs_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)V, N, r, tr, partial);
+  } else {
+    size_t bytes = 5 * (size_t)tr * r * sizeof(cx<float>) + nent * 16;
+    ::lrei::count_launch(); obs_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)V, N, r, tr, partial);
+  }
+  return grid;
+}
+
+
 // ------------------------------------------------------ conversion / checks
 template <typename S, typename D>
 __global__ void convert_kernel(const cx<S> *src, int ld, cx<D> *dst, long long N, int r) {
