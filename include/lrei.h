@@ -148,6 +148,15 @@ const char *lrei_error_string(int code);
  * ld = r, dtype must match the context's precision.  V_dev != Y_dev. */
 int lrei_apply_h(lrei_ctx *ctx, const void *V_dev, void *Y_dev, int r);
 
+/* Tall-skinny Gram P = [B_0, ..., B_{m-1}]^* B_{m-1} (the V^*W-type products of
+ * Sec. 3.5-3.7: projections onto the current basis and the Gram of the newest
+ * block), by the same fused tile pass and deterministic reduction the step uses.
+ * blocks_dev: m device pointers (1 <= m <= 13), each N x r row-major with the
+ * context's r and precision; G_dev: device complex128 (m r) x r, column-major,
+ * written on the context's stream (no host sync).  Compensated FP32 sums in
+ * mixed precision, FP64 otherwise. */
+int lrei_gram(lrei_ctx *ctx, const void *const *blocks_dev, int nblocks, void *G_dev);
+
 /* Low-rank right-hand side at the current state: f(rho) = Z V^* + V W^*
  * (Sec. 3.5 eq. q-LLG-low-rank; q-LL blocks of Sec. 4).  Writes Z and W
  * (N x r each, device, ld = r, the context's dtype) and, if G_host is not

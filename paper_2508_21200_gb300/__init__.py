@@ -80,6 +80,7 @@ def load_library(path: str | None = None):
         "lrei_destroy": (I, [P]),
         "lrei_error_string": (ctypes.c_char_p, [I]),
         "lrei_apply_h": (I, [P, P, P, I]),
+        "lrei_gram": (I, [P, P, I, P]),
         "lrei_rhs": (I, [P, P, P, ctypes.POINTER(D), I]),
         "lrei_householder": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "lrei_kernel_launches": (L, [P]),
@@ -198,6 +199,18 @@ class Lrei:
         assert V.is_contiguous() and Y.is_contiguous()
         _check(self._lib.lrei_apply_h(self._h, ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                       V.shape[1]))
+
+    def gram(self, blocks, out=None):
+        """P = [B_0..B_{m-1}]^* B_{m-1} as a (m r) x r complex128 device tensor (no host sync)."""
+        import torch
+        m = len(blocks)
+        for b in blocks:
+            assert b.is_contiguous() and b.dtype == self.torch_dtype and tuple(b.shape) == (self.N, self.r)
+        ptrs = (ctypes.c_void_p * m)(*[b.data_ptr() for b in blocks])
+        if out is None:
+            out = torch.empty((self.r, m * self.r), dtype=torch.complex128, device="cuda")   # column-major (m r) x r
+        _check(self._lib.lrei_gram(self._h, ptrs, m, ctypes.c_void_p(out.data_ptr())), self._h)
+        return out.T
 
     def rhs(self, complement=0):
         import torch

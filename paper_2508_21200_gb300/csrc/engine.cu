@@ -1237,6 +1237,7 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
   int rejected_in_row = 0;
   int since_judge = c->ctrl_judge_every;   // the first step is judged
   bool last_rejected = false;
+  bool net_chose_h = false;   // the step being taken has the size the network proposed
   int accepted_flag = 1;
   double f[3];
   while (c->t < t_end - 1e-12 * std::fmax(1.0, std::fabs(t_end))) {
@@ -1278,7 +1279,10 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       h = hs * std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2));
       last_rejected = true;
       accepted_flag = 0;
-      if (controller == 1 && do_judge) c->learned_fallback = 16;
+      // a rejected step whose size came from the network (by the judge or by the drift
+      // estimate) hands control to the plain rule for the next 16 steps
+      if (controller == 1 && (do_judge || net_chose_h)) c->learned_fallback = 16;
+      net_chose_h = false;
       if (++rejected_in_row >= 64 || h < h_min) {
         c->ctrl_h = h;
         return LREI_ERR_STEP;
@@ -1291,6 +1295,7 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
     last_rejected = false;
     accepted_flag = 1;
     double ratio = std::fmin(5.0, std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2)));
+    net_chose_h = false;
     if (controller == 1 && c->net && c->learned_fallback <= 0) {
       float x[NFEAT];
       build_features(c, f, hs, tol, x);
@@ -1301,7 +1306,10 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       LREI_CUDA_TRY(cudaMemcpyAsync(c->net_host, c->net_y, sizeof(float), cudaMemcpyDeviceToHost, c->st));
       LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
       const double pred = std::exp((double)c->net_host[0]);
-      if (std::isfinite(pred)) ratio = std::fmin(5.0, std::fmax(0.2, pred));
+      if (std::isfinite(pred)) {
+        ratio = std::fmin(2.0, std::fmax(0.2, pred));   // growth capped at 2x per step
+        net_chose_h = true;
+      }
     }
     if (c->learned_fallback > 0) --c->learned_fallback;
     h = hs * ratio;
@@ -1678,6 +1686,34 @@ int lrei_apply_h(lrei_ctx *c, const void *V_dev, void *Y_dev, int r) {
   leave(c);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LREI_OK : cuda_fail(e, "apply_h");
+}
+
+int lrei_gram(lrei_ctx *c, const void *const *blocks_dev, int nblocks, void *G_dev) {
+  if (!c || !blocks_dev || !G_dev || nblocks < 1 || nblocks > MAXB + 1) return LREI_ERR_ARG;
+  for (int i = 0; i < nblocks; ++i)
+    if (!blocks_dev[i]) return LREI_ERR_ARG;
+  const int r = c->r;
+  if (r < 1) return LREI_ERR_STATE;
+  enter(c);
+  TSArgs a{};
+  a.nq = nblocks - 1;
+  a.gram_left = nblocks - 1;
+  for (int i = 0; i + 1 < nblocks; ++i) a.q[i] = const_cast<void *>(blocks_dev[i]);
+  a.src = const_cast<void *>(blocks_dev[nblocks - 1]);
+  a.apply_h = 0;
+  a.mode = 0;
+  int rc = ts_pass(c, a);
+  if (!rc) {
+    const size_t bytes = (size_t)nblocks * r * r * sizeof(zd);
+    cudaError_t e = cudaMemcpyAsync(G_dev, c->red, bytes, cudaMemcpyDeviceToDevice, c->st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "gram");
+  }
+  leave(c);
+  if (!rc) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "gram");
+  }
+  return rc;
 }
 
 // Householder compact-WY factors of the current factor (U into U_dev, T and D to the host).

@@ -229,7 +229,7 @@ struct Rot {
 template <typename T>
 __global__ void __launch_bounds__(512) jacobi_kernel(const zd *__restrict__ Ain, int lda, int k, zd *__restrict__ Uout,
                                                      int ldu, double *__restrict__ wout, cx<T> *Ug, int max_sweeps,
-                                                     double tol, int *status) {
+                                                     double tol, int *status, cx<float> *__restrict__ Uf, int nout) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int kp = k + (k & 1);
   const int np = kp / 2;
@@ -251,14 +251,16 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const zd *__restrict__ Ain,
   }
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence test: off-diagonal vs total Frobenius norm
-    double off = 0.0, tot = 0.0;
+    // convergence test: off-diagonal vs total Frobenius norm (summed in T per thread: the FP32
+    // solver's test needs no FP64 arithmetic, which is slow on this part)
+    T offt = 0, tott = 0;
     for (int e = t; e < kp * kp; e += nt) {
       const int i = e % kp, j = e / kp;
-      const double v = (double)norm2(A[e]);
-      tot += v;
-      if (i != j) off += v;
+      const T v = norm2(A[e]);
+      tott += v;
+      if (i != j) offt += v;
     }
+    double off = (double)offt, tot = (double)tott;
     for (int o = 16; o > 0; o >>= 1) {
       off += __shfl_xor_sync(0xffffffffu, off, o);
       tot += __shfl_xor_sync(0xffffffffu, tot, o);
@@ -349,10 +351,16 @@ __global__ void __launch_bounds__(512) jacobi_kernel(const zd *__restrict__ Ain,
       rank += (wj > wi) || (wj == wi && j < i);
     }
     wout[rank] = (double)wi;
-    for (int row = 0; row < k; ++row) {
-      const cx<T> u = U[(size_t)i * kp + row];
-      Uout[(size_t)rank * ldu + row] = mk<double>((double)u.re, (double)u.im);
-    }
+    if (rank < nout)
+      for (int row = 0; row < k; ++row) {
+        const cx<T> u = U[(size_t)i * kp + row];
+        Uout[(size_t)rank * ldu + row] = mk<double>((double)u.re, (double)u.im);
+      }
+    if (Uf)
+      for (int row = 0; row < k; ++row) {
+        const cx<T> u = U[(size_t)i * kp + row];
+        Uf[(size_t)rank * k + row] = mk<float>((float)u.re, (float)u.im);
+      }
   }
 }
 
@@ -368,18 +376,19 @@ size_t sm_jacobi_scratch_bytes(int k) {
 }
 
 void sm_jacobi(bool fp64, const zd *A, int lda, int k, zd *U, int ldu, double *w, void *scratch, int max_sweeps,
-               double tol, int *status, cudaStream_t st) {
+               double tol, int *status, cudaStream_t st, void *Uf32, int nout) {
   const size_t lim = 200 * 1024;
+  if (nout < 0 || nout > k) nout = k;
   if (fp64) {
     const bool in_smem = jacobi_smem<double>(k, true) <= lim;
     const size_t bytes = jacobi_smem<double>(k, in_smem);
     ::lrei::count_launch(); jacobi_kernel<double><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<double> *)scratch,
-                                                 max_sweeps, tol, status);
+                                                 max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
   } else {
     const bool in_smem = jacobi_smem<float>(k, true) <= lim;
     const size_t bytes = jacobi_smem<float>(k, in_smem);
     ::lrei::count_launch(); jacobi_kernel<float><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
-                                                max_sweeps, tol, status);
+                                                max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
   }
 }
 
@@ -390,21 +399,111 @@ void sm_jacobi(bool fp64, const zd *A, int lda, int k, zd *U, int ldu, double *w
 // other k - r eigenvalues.  Because the correction is driven by the residual (which vanishes
 // exactly on the invariant subspace), repeated passes converge to FP64 accuracy even though Ur
 // is only FP32-accurate.
-__global__ void newton_scale_kernel(zd *__restrict__ A21, int lda21, const zd *__restrict__ A11, int r,
-                                    const double *__restrict__ w, int k) {
-  const int j = blockIdx.x;
-  const double d = A11[(size_t)j * r + j].re;
-  for (int i = threadIdx.x; i < k - r; i += blockDim.x) {
-    const double den = d - w[r + i];
-    const zd a = A21[(size_t)j * lda21 + i];
-    A21[(size_t)j * lda21 + i] = (fabs(den) > 1e-300) ? mk<double>(a.re / den, a.im / den) : mk<double>(0, 0);
+// One CTA per column j of E; every step below is local to that column once W1 = M E is known:
+//   a = E^H W1[:, j],  R = W1[:, j] - E a                  (FP64: the residual is a small difference)
+//   X_i = (Ur^H R)_i / (a_j - w_{r+i}),  D = Ur X           (FP32: only the correction's leading digits
+//   Enew[:, j] = E[:, j] + D - E (E^H D)                      matter; Ur is FP32-accurate anyway)
+// Ur is read from the FP32 eigenvectors (k x k, ld k, column r + i).  E is read by all CTAs, so the
+// result goes to a separate array.  FP64 work is kept to the residual: on this part FP64
+// (including conversions) runs at 1/58 of the FP32 rate.
+__global__ void __launch_bounds__(256) newton_chain_kernel(const zd *__restrict__ W1, int ldw, const zd *__restrict__ E,
+                                                           int lde, const cx<float> *__restrict__ Uf,
+                                                           const double *__restrict__ w, int k, int r,
+                                                           zd *__restrict__ Enew, int ldn) {
+  extern __shared__ __align__(16) unsigned char nsm[];
+  zd *w1 = reinterpret_cast<zd *>(nsm);                    // k
+  zd *av = w1 + k;                                          // r
+  cx<float> *rf = reinterpret_cast<cx<float> *>(av + r);    // k: residual (FP32)
+  cx<float> *x = rf + k;                                    // k - r
+  cx<float> *d2 = x + k;                                    // k
+  cx<float> *ef = d2 + k;                                   // k x r: E in FP32 (for the projection)
+  cx<float> *g1 = ef + (size_t)k * r;                       // r
+  const int j = blockIdx.x, t = threadIdx.x, lane = t & 31, wp = t >> 5, nw = blockDim.x >> 5;
+  for (int p = t; p < k; p += blockDim.x) w1[p] = W1[(size_t)j * ldw + p];
+  __syncthreads();
+  for (int i = wp; i < r; i += nw) {          // a = E^H w1
+    zd s = mk<double>(0, 0);
+    for (int p = lane; p < k; p += 32) fmac_(s, E[(size_t)i * lde + p], w1[p]);
+    s = warp_sum(s);
+    if (lane == 0) av[i] = s;
+  }
+  __syncthreads();
+  for (int p = t; p < k; p += blockDim.x) {   // R = w1 - E a; E to FP32 for the projection below
+    zd s = w1[p];
+    for (int i = 0; i < r; ++i) {
+      const zd e = E[(size_t)i * lde + p];
+      s = s - e * av[i];
+      ef[(size_t)i * k + p] = cvt<float>(e);
+    }
+    rf[p] = cvt<float>(s);
+  }
+  __syncthreads();
+  const double dj = av[j].re;
+  for (int i = wp; i < k - r; i += nw) {      // X = (Ur^H R) ./ (d_j - w)
+    cx<float> s = mk<float>(0.f, 0.f);
+    const cx<float> *u = Uf + (size_t)(r + i) * k;
+    for (int p = lane; p < k; p += 32) fmac_(s, u[p], rf[p]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
+      s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
+    }
+    if (lane == 0) {
+      const float den = (float)(dj - w[r + i]);
+      x[i] = (fabsf(den) > 1e-30f) ? mk<float>(s.re / den, s.im / den) : mk<float>(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  for (int p = t; p < k; p += blockDim.x) {   // D = Ur X
+    cx<float> s = mk<float>(0.f, 0.f);
+#pragma unroll 8
+    for (int i = 0; i < k - r; ++i) fma_(s, Uf[(size_t)(r + i) * k + p], x[i]);
+    d2[p] = s;
+  }
+  __syncthreads();
+  for (int i = wp; i < r; i += nw) {          // g = E^H D
+    cx<float> s = mk<float>(0.f, 0.f);
+    for (int p = lane; p < k; p += 32) fmac_(s, ef[(size_t)i * k + p], d2[p]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s.re += __shfl_xor_sync(0xffffffffu, s.re, o);
+      s.im += __shfl_xor_sync(0xffffffffu, s.im, o);
+    }
+    if (lane == 0) g1[i] = s;
+  }
+  __syncthreads();
+  for (int p = t; p < k; p += blockDim.x) {   // Enew = E + D - E g
+    cx<float> s = d2[p];
+    for (int i = 0; i < r; ++i) s = s - ef[(size_t)i * k + p] * g1[i];
+    const zd e = E[(size_t)j * lde + p];
+    Enew[(size_t)j * ldn + p] = mk<double>(e.re + (double)s.re, e.im + (double)s.im);
   }
 }
 
-__global__ void add_kernel(zd *__restrict__ E, int lde, const zd *__restrict__ D, int ldd, int k, int r) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * r; e += gridDim.x * blockDim.x) {
-    const int i = e % k, j = e / k;
-    E[(size_t)j * lde + i] = E[(size_t)j * lde + i] + D[(size_t)j * ldd + i];
+size_t newton_chain_smem(int k, int r) {
+  return (size_t)(k + r) * sizeof(zd) + (size_t)(3 * k + (size_t)k * r + r) * sizeof(cx<float>) + 64;
+}
+
+// T = (15/8) I - (5/4) G + (3/8) G^2 for G = E^H E = I + d: then E T = E (E^H E)^{-1/2} + O(d^3),
+// the orthonormal polar factor of E (same span).  One CTA per column j; the sum over m of
+// (G^2)_{ij} is split over the CTA's threads and combined in shared memory.
+__global__ void __launch_bounds__(256) polar_t_kernel(const zd *__restrict__ G, int ldg, int r, zd *__restrict__ T,
+                                                      int ldt) {
+  __shared__ zd part[256];
+  const int j = blockIdx.x, t = threadIdx.x;
+  const int i = t % r, q = t / r, nq = blockDim.x / r;
+  zd s = mk<double>(0, 0);
+  if (q < nq)
+    for (int m = q; m < r; m += nq) fma_(s, G[(size_t)m * ldg + i], G[(size_t)j * ldg + m]);
+  part[t] = s;
+  __syncthreads();
+  if (t < r) {
+    zd g2 = mk<double>(0, 0);
+    for (int u = 0; u < nq; ++u) g2 = g2 + part[u * r + t];
+    const zd gij = G[(size_t)j * ldg + t];
+    zd v = mk<double>(-1.25 * gij.re + 0.375 * g2.re, -1.25 * gij.im + 0.375 * g2.im);
+    if (t == j) v.re += 1.875;
+    T[(size_t)j * ldt + t] = v;
   }
 }
 
@@ -437,12 +536,12 @@ __global__ void eig_check_kernel(const zd *__restrict__ MY, int ldmy, const zd *
 size_t sm_eig_ws_bytes(int kmax, int rmax) {
   size_t z = sizeof(zd);
   size_t b = 0;
-  b += (size_t)kmax * kmax * z;      // U
   b += (size_t)kmax * 8;             // w
   b += 4 * (size_t)kmax * rmax * z;  // W1, A21, E1, W2
   b += 4 * (size_t)rmax * rmax * z;  // G1, L1, Ar, Wr
   b += sm_jacobi_scratch_bytes(kmax);
   b += (size_t)rmax * rmax * z + (size_t)kmax * rmax * z;
+  b += (size_t)kmax * kmax * sizeof(cx<float>) + 256;   // FP32 eigenvectors
   return b + 4096;
 }
 
@@ -450,7 +549,6 @@ void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu,
                  cudaStream_t st) {
   unsigned char *p = reinterpret_cast<unsigned char *>(ws);
   auto take = [&](size_t bytes) { unsigned char *q = p; p += (bytes + 255) & ~(size_t)255; return q; };
-  zd *U = (zd *)take((size_t)k * k * sizeof(zd));
   double *w = (double *)take((size_t)k * 8);
   zd *W1 = (zd *)take((size_t)k * r * sizeof(zd));
   zd *A21 = (zd *)take((size_t)k * r * sizeof(zd));
@@ -463,29 +561,28 @@ void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu,
   void *jscratch = take(sm_jacobi_scratch_bytes(k));
   zd *Inv = (zd *)take((size_t)r * r * sizeof(zd));
   zd *Xc = (zd *)take((size_t)k * r * sizeof(zd));
+  cx<float> *U32 = (cx<float> *)take((size_t)k * k * sizeof(cx<float>));
   const zd one = mk<double>(1, 0), zero = mk<double>(0, 0);
-  // 1. FP32 eigendecomposition of the whole k x k matrix
-  sm_jacobi(false, M, ldm, k, U, k, w, jscratch, 12, 1e-5, nullptr, st);
-  // 2.-3. block-Newton corrections of the top-r invariant subspace, each followed by an
-  // FP64 Cholesky-QR re-orthonormalisation of E1
-  sm_copy(U, k, k, r, E1, k, st);
-  const zd mone = mk<double>(-1, 0);
+  (void)Inv; (void)Xc; (void)A21; (void)L1;
+  // 1. FP32 eigendecomposition of the whole k x k matrix: all eigenvectors in FP32 (U32), the
+  //    top r also in FP64 (E1), eigenvalues in FP64 (w)
+  sm_jacobi(false, M, ldm, k, E1, k, w, jscratch, 12, 1e-5, nullptr, st, U32, r);
+  // 2.-3. block-Newton corrections of the top-r invariant subspace, each followed by the polar
+  // re-orthonormalisation E <- E T, T = (E^H E)^{-1/2} to third order (multi-CTA FP64 gemms)
   const int passes = (k > r) ? 4 : 1;
   for (int it = 0; it < passes; ++it) {
+    zd *Ecur = E1;
     if (k > r) {
       sm_gemm('N', 'N', k, r, k, one, M, ldm, E1, k, zero, W1, k, st);           // W1 = M E
-      sm_gemm('C', 'N', r, r, k, one, E1, k, W1, k, zero, Ar, r, st);            // A11 = E^H M E
-      sm_gemm('N', 'N', k, r, r, mone, E1, k, Ar, r, one, W1, k, st);           // R = M E - E A11
-      sm_gemm('C', 'N', k - r, r, k, one, U + (size_t)r * k, k, W1, k, zero, A21, k, st);   // Ur^H R
-      ::lrei::count_launch(); newton_scale_kernel<<<r, 64, 0, st>>>(A21, k, Ar, r, w, k);               // X
-      sm_gemm('N', 'N', k, r, k - r, one, U + (size_t)r * k, k, A21, k, zero, W2, k, st);    // D = Ur X
-      sm_gemm('C', 'N', r, r, k, one, E1, k, W2, k, zero, G1, r, st);            // E^H D
-      sm_gemm('N', 'N', k, r, r, mone, E1, k, G1, r, one, W2, k, st);           // D -= E (E^H D)
-      ::lrei::count_launch(); add_kernel<<<8, 256, 0, st>>>(E1, k, W2, k, k, r);                        // E += D
+      ::lrei::count_launch();
+      newton_chain_kernel<<<r, 256, newton_chain_smem(k, r), st>>>(W1, k, E1, k, U32, w, k, r, W2, k);
+      Ecur = W2;
     }
-    sm_gemm('C', 'N', r, r, k, one, E1, k, E1, k, zero, G1, r, st);
-    sm_chol(G1, r, r, L1, r, 0.0, 0, nullptr, nullptr, 0, st, nullptr, 0);
-    sm_rtrsm_lh_ws(E1, k, k, L1, r, r, Inv, Xc, st);
+    sm_gemm('C', 'N', r, r, k, one, Ecur, k, Ecur, k, zero, G1, r, st);         // G = E^H E
+    ::lrei::count_launch();
+    polar_t_kernel<<<r, 256, 0, st>>>(G1, r, r, Ar, r);                        // T
+    sm_gemm('N', 'N', k, r, r, one, Ecur, k, Ar, r, zero, (Ecur == E1) ? W2 : E1, k, st);
+    if (Ecur == E1) sm_copy(W2, k, k, r, E1, k, st);
   }
   // 4. Rayleigh-Ritz on span(E1) in FP64
   sm_gemm('N', 'N', k, r, k, one, M, ldm, E1, k, zero, W2, k, st);
@@ -566,7 +663,8 @@ int sm_init() {
   cudaFuncSetAttribute(trsv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t a = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t b = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  return (a == cudaSuccess && b == cudaSuccess) ? 0 : -1;
+  cudaError_t c = cudaFuncSetAttribute(newton_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess) ? 0 : -1;
 }
 }  // namespace lrei
 

@@ -31,7 +31,7 @@ void sm_chol(const zd *A, int lda, int k, zd *L, int ldl, double tol, int zero_r
 // Hermitian eigendecomposition by cyclic Jacobi in working precision T (float or double),
 // one CTA.  Eigenvalues w sorted decreasing (ties by index), eigenvectors U (k x k, FP64).
 void sm_jacobi(bool fp64, const zd *A, int lda, int k, zd *U, int ldu, double *w, void *scratch, int max_sweeps,
-               double tol, int *status, cudaStream_t st);
+               double tol, int *status, cudaStream_t st, void *Uf32 = nullptr, int nout = -1);
 size_t sm_jacobi_scratch_bytes(int k);
 
 // Top-r eigenpairs of the Hermitian k x k matrix M to FP64 accuracy: FP32 Jacobi, one

@@ -184,6 +184,109 @@ __global__ void __launch_bounds__(256) hv2_kernel(const __grid_constant__ ModelA
   }
 }
 
+// ------------------------------------------------ H.V, slab-major, swizzled shared tiles
+// Same traversal as hv2_kernel (slab by slab, so the slab being processed stays resident in L2
+// and partner rows outside the tile are L2 hits).  The tile is held as 16-byte chunks; the two
+// halves of a row swap places in every other group of four rows, so the 8 lanes of a
+// quarter-warp reading 8 aligned rows (or any XOR image of them, which is what a bit-flip
+// partner lookup reads) touch 8 distinct bank groups with 128-bit loads.  Bonds are taken four
+// at a time: the four partner loads (shared or global) are issued before their multiply-adds,
+// so up to four L2 round trips per row are in flight together.
+// A 32-byte slab row as two 16-byte chunks, read as real words of type T.
+struct Row32 {
+  float4 v[2];
+};
+template <typename T> __device__ __forceinline__ T row_word(const Row32 &x, int q);
+template <> __device__ __forceinline__ float row_word<float>(const Row32 &x, int q) {
+  const float4 &c = x.v[q >> 2];
+  const int i = q & 3;
+  return i == 0 ? c.x : (i == 1 ? c.y : (i == 2 ? c.z : c.w));
+}
+template <> __device__ __forceinline__ double row_word<double>(const Row32 &x, int q) {
+  const float4 &c = x.v[q >> 1];
+  return (q & 1) ? __hiloint2double(__float_as_int(c.w), __float_as_int(c.z))
+                 : __hiloint2double(__float_as_int(c.y), __float_as_int(c.x));
+}
+template <typename T> __device__ __forceinline__ void row_set(Row32 &x, const T (&w)[32 / sizeof(T)]);
+template <> __device__ __forceinline__ void row_set<float>(Row32 &x, const float (&w)[8]) {
+  x.v[0] = make_float4(w[0], w[1], w[2], w[3]);
+  x.v[1] = make_float4(w[4], w[5], w[6], w[7]);
+}
+template <> __device__ __forceinline__ void row_set<double>(Row32 &x, const double (&w)[4]) {
+  x.v[0] = make_float4(__int_as_float(__double2loint(w[0])), __int_as_float(__double2hiint(w[0])),
+                       __int_as_float(__double2loint(w[1])), __int_as_float(__double2hiint(w[1])));
+  x.v[1] = make_float4(__int_as_float(__double2loint(w[2])), __int_as_float(__double2hiint(w[2])),
+                       __int_as_float(__double2loint(w[3])), __int_as_float(__double2hiint(w[3])));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) hv3_kernel(const __grid_constant__ ModelArgs M, const cx<T> *__restrict__ X,
+                                                  cx<T> *__restrict__ Y, long long N, int r, int tbits) {
+  constexpr int SW = 32 / sizeof(cx<T>);   // complex elements per slab row
+  constexpr int NW = 32 / sizeof(T);       // real words per slab row
+  extern __shared__ __align__(16) float4 hv3_tile[];
+  const uint32_t TR = 1u << tbits;
+  const long long ntile = N >> tbits;
+  const int slab = (int)(blockIdx.x / ntile);
+  const uint32_t t0 = (uint32_t)((blockIdx.x % ntile) << tbits);
+  const int c0 = slab * SW;
+  for (uint32_t e = threadIdx.x; e < 2 * TR; e += blockDim.x) {
+    const uint32_t lr = e >> 1, h = e & 1u;
+    hv3_tile[2 * lr + (h ^ ((lr >> 2) & 1u))] =
+        __ldg(reinterpret_cast<const float4 *>(X + (size_t)(t0 + lr) * r + c0) + h);
+  }
+  __syncthreads();
+  for (uint32_t lr = threadIdx.x; lr < TR; lr += blockDim.x) {
+    const uint32_t b = t0 + lr;
+    T diag = (T)(M.c0 + M.bz * (0.5 * M.n - (double)__popc(b)));
+    T acc[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) acc[q] = (T)0;
+    for (int k0 = 0; k0 < M.nb; k0 += 4) {
+      Row32 p[4];
+      T jj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u;
+        jj[u] = (T)0;
+        p[u].v[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p[u].v[1] = p[u].v[0];
+        if (k < M.nb && (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u)) {
+          diag -= (T)M.jz[k];
+          jj[u] = (T)M.jxy[k];
+          const uint32_t mk = M.mask[k];
+          if (mk < TR) {
+            const uint32_t pr = lr ^ mk, s = (pr >> 2) & 1u;
+            p[u].v[0] = hv3_tile[2 * pr + s];
+            p[u].v[1] = hv3_tile[2 * pr + (s ^ 1u)];
+          } else {
+            const float4 *g = reinterpret_cast<const float4 *>(X + (size_t)(b ^ mk) * r + c0);
+            p[u].v[0] = __ldg(g);
+            p[u].v[1] = __ldg(g + 1);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < NW; ++q) acc[q] = fma(jj[u], row_word<T>(p[u], q), acc[q]);
+    }
+    Row32 own, o;
+    {
+      const uint32_t s = (lr >> 2) & 1u;
+      own.v[0] = hv3_tile[2 * lr + s];
+      own.v[1] = hv3_tile[2 * lr + (s ^ 1u)];
+    }
+    T ow[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) ow[q] = fma(diag, row_word<T>(own, q), acc[q]);
+    row_set<T>(o, ow);
+    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)b * r + c0);
+    dst[0] = o.v[0];
+    dst[1] = o.v[1];
+  }
+}
+
 // ------------------------------------------------------ accumulation
 // Error-free sum: s + e == a + b exactly (Knuth TwoSum).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
@@ -217,6 +320,7 @@ template <> struct Acc<float> {
 // ------------------------------------------------------ fused tile pass
 constexpr int TS_THREADS = 256;
 static bool g_force_v1 = false;   // selects the unblocked kernel (A/B comparison)
+static bool g_hv_v2 = false;       // selects the unswizzled slab-major H.V kernel (A/B comparison)
 
 
 template <typename T>
@@ -553,6 +657,194 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
   (void)lane;
 }
 
+// ------------------------------------------- fused tile pass, pipelined (complex64 bulk)
+// Same contract as ts_kernel for T = float, split H.V (apply_h == 0) and r in {8, 16, 32}.
+// Each CTA walks its tiles of TR rows with the next tile's blocks already in flight: cp.async
+// copies the rows of every input block into the other half of a double buffer (padded rows,
+// RS = r + 2 complex, so that rows of one column fall in different banks) while the current
+// tile is computed.  Gram work split: a micro-tile is column c of every Gram block against 4
+// consecutive G columns (g x 4 complex accumulators); NPH lanes of one warp take interleaved
+// rows of the same micro-tile and are combined by shuffles at each flush, every FLUSHT tiles,
+// into compensated FP32 pairs (TwoSum) in shared memory.  Lane = phase * TPW + micro-tile, so
+// the G loads of a quarter-warp are one row (distinct 16-byte columns) and the block loads of
+// a half-warp are two rows of two columns: no bank conflicts at r = 16.
+template <int R, int TR, int GMAX>
+__global__ void __launch_bounds__(256, (TR <= 32 ? 2 : 1)) ts3_kernel(const __grid_constant__ TSArgs a,
+                                                                     const cx<float> *__restrict__ coefg) {
+  constexpr int RS = R + 2;
+  constexpr int MTS = R * R / 4;
+  constexpr int NPH = 256 / MTS;
+  constexpr int TPW = 32 / NPH;
+  constexpr int CH = R / 2;                 // 16-byte chunks per row
+  constexpr int FLUSHT = 8;                 // GMAX: Gram blocks this instance handles (gl + 1 <= GMAX)
+  static_assert(NPH >= 1 && NPH <= 32 && (32 % NPH) == 0 && (RS * 8) % 16 == 0, "r in {8, 16, 32}");
+  extern __shared__ __align__(16) unsigned char smem3[];
+  const int nq = a.nq, gl = a.gram_left, mode = a.mode;
+  const int nb = nq + (mode != 2 ? 1 : 0);
+  const int g = gl + 1;
+  const int bstride = TR * RS;
+  cx<float> *buf = reinterpret_cast<cx<float> *>(smem3);       // [2][nb][TR][RS]
+  cx<float> *ns = buf + 2 * nb * bstride;                       // [TR][RS] new tile
+  cx<float> *cs = ns + bstride;                                 // [(nq+1) R][R] coefficients
+  float *slots = reinterpret_cast<float *>(cs + (mode != 0 ? (nq + 1) * R * R : 0));   // [g R][R][4]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ph = lane / TPW;
+  const int mt = warp * TPW + lane % TPW;
+  const int c = mt / (R / 4), j0 = (mt % (R / 4)) * 4;
+  const long long N = a.N;
+  const long long ntiles = (N + TR - 1) / TR;
+
+  if (mode != 0)
+    for (int e = tid; e < (nq + 1) * R * R; e += 256) cs[e] = coefg[e];
+  for (int e = tid; e < g * R * R * 4; e += 256) slots[e] = 0.f;
+
+  auto prefetch = [&](long long tile, int sb) {
+    const long long row0 = tile * TR;
+    for (int m = 0; m < nb; ++m) {
+      const cx<float> *base = reinterpret_cast<const cx<float> *>(m < nq ? a.q[m] : a.src);
+      cx<float> *dst = buf + (size_t)(sb * nb + m) * bstride;
+      for (int e = tid; e < TR * CH; e += 256) {
+        const int lr = e / CH, ch = e % CH;
+        const bool ok = row0 + lr < N;
+        const cx<float> *gp = ok ? base + (size_t)(row0 + lr) * R + ch * 2 : base;
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(dst + lr * RS + ch * 2);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gp), "r"(ok ? 16 : 0));
+      }
+    }
+  };
+
+  cx<float> acc[GMAX][4];
+#pragma unroll
+  for (int m = 0; m < GMAX; ++m)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[m][y] = mk<float>(0.f, 0.f);
+
+  auto flush = [&]() {
+#pragma unroll
+    for (int m = 0; m < GMAX; ++m) {
+      if (m < g) {
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          float re = acc[m][y].re, im = acc[m][y].im;
+#pragma unroll
+          for (int o = TPW; o < 32; o <<= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+          }
+          if (ph == 0) {
+            float *s = slots + ((size_t)(m * R + c) * R + j0 + y) * 4;
+            two_sum_acc(s[0], s[1], re);
+            two_sum_acc(s[2], s[3], im);
+          }
+          acc[m][y] = mk<float>(0.f, 0.f);
+        }
+      }
+    }
+  };
+
+  long long tile = blockIdx.x;
+  int sb = 0;
+  if (tile < ntiles) prefetch(tile, 0);
+  asm volatile("cp.async.commit_group;\n" ::);
+  int since = 0;
+  for (; tile < ntiles; tile += gridDim.x) {
+    const long long nxt = tile + gridDim.x;
+    if (nxt < ntiles) prefetch(nxt, sb ^ 1);
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 1;\n" ::);
+    __syncthreads();
+    const cx<float> *B0 = buf + (size_t)sb * nb * bstride;
+    const long long row0 = tile * TR;
+    const int rows = (int)((N - row0) < TR ? (N - row0) : TR);
+    const cx<float> *G;
+    if (mode != 0) {
+      const int mlast = (mode == 1) ? nq : nq - 1;
+      cx<float> *out = reinterpret_cast<cx<float> *>(a.out);
+      for (int e = tid; e < TR * (R / 4); e += 256) {
+        const int lr = e / (R / 4), q0 = (e % (R / 4)) * 4;
+        cx<float> o[4];
+#pragma unroll
+        for (int y = 0; y < 4; ++y) o[y] = mk<float>(0.f, 0.f);
+        for (int m = 0; m <= mlast; ++m) {
+          const cx<float> *X = B0 + (size_t)m * bstride + lr * RS;
+          const cx<float> *C = cs + (size_t)m * R * R + q0;
+#pragma unroll 4
+          for (int i = 0; i < R; ++i) {
+            const cx<float> x = X[i];
+            const float4 c01 = *reinterpret_cast<const float4 *>(C + i * R);
+            const float4 c23 = *reinterpret_cast<const float4 *>(C + i * R + 2);
+            fma_(o[0], x, mk<float>(c01.x, c01.y));
+            fma_(o[1], x, mk<float>(c01.z, c01.w));
+            fma_(o[2], x, mk<float>(c23.x, c23.y));
+            fma_(o[3], x, mk<float>(c23.z, c23.w));
+          }
+        }
+        const bool valid = lr < rows && row0 + lr >= a.zero_rows;
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if (!valid) o[y] = mk<float>(0.f, 0.f);
+        float4 *nd = reinterpret_cast<float4 *>(ns + lr * RS + q0);
+        nd[0] = make_float4(o[0].re, o[0].im, o[1].re, o[1].im);
+        nd[1] = make_float4(o[2].re, o[2].im, o[3].re, o[3].im);
+        if (out && lr < rows) {
+          float4 *od = reinterpret_cast<float4 *>(out + (size_t)(row0 + lr) * R + q0);
+          od[0] = nd[0];
+          od[1] = nd[1];
+        }
+      }
+      __syncthreads();
+      G = ns;
+    } else {
+      G = B0 + (size_t)nq * bstride;
+    }
+#pragma unroll 2
+    for (int lr = ph; lr < TR; lr += NPH) {
+      const float4 ga = *reinterpret_cast<const float4 *>(G + lr * RS + j0);
+      const float4 gb = *reinterpret_cast<const float4 *>(G + lr * RS + j0 + 2);
+      const cx<float> gv0 = mk<float>(ga.x, ga.y), gv1 = mk<float>(ga.z, ga.w);
+      const cx<float> gv2 = mk<float>(gb.x, gb.y), gv3 = mk<float>(gb.z, gb.w);
+#pragma unroll
+      for (int m = 0; m < GMAX; ++m) {
+        if (m < g) {
+          const cx<float> *L = (m < gl) ? B0 + (size_t)m * bstride : G;
+          const cx<float> lv = L[lr * RS + c];
+          fmac_(acc[m][0], lv, gv0);
+          fmac_(acc[m][1], lv, gv1);
+          fmac_(acc[m][2], lv, gv2);
+          fmac_(acc[m][3], lv, gv3);
+        }
+      }
+    }
+    if (++since >= FLUSHT) {
+      since = 0;
+      flush();
+    }
+    __syncthreads();
+    sb ^= 1;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+  flush();
+  __syncthreads();
+  const int ldg_ = g * R, nent = ldg_ * R;
+  double *outp = a.partial + (size_t)blockIdx.x * nent * 2;
+  for (int e = tid; e < nent; e += 256) {
+    const int j = e / ldg_, row = e % ldg_;
+    const float *s = slots + ((size_t)row * R + j) * 4;
+    outp[2 * e] = (double)s[0] + (double)s[1];
+    outp[2 * e + 1] = (double)s[2] + (double)s[3];
+  }
+}
+
+template <int R, int TR>
+__host__ inline size_t ts3_bytes(int nq, int gl, int mode) {
+  const int nb = nq + (mode != 2 ? 1 : 0);
+  const size_t bstride = (size_t)TR * (R + 2) * sizeof(cx<float>);
+  size_t b = (2 * (size_t)nb + 1) * bstride;
+  if (mode != 0) b += (size_t)(nq + 1) * R * R * sizeof(cx<float>);
+  b += (size_t)(gl + 1) * R * R * 16;
+  return b;
+}
+
 // Coefficients in the padded row-major layout of ts2_kernel: row m*rp + i, column j.
 template <typename T>
 __global__ void coef_convert2_kernel(const zd *coefQ, const zd *coefS, int nq, int r, int mode, cx<T> *out) {
@@ -636,8 +928,81 @@ static int launch_ts_v1(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream
   return grid;
 }
 
+static bool g_force_ts2 = false;   // selects the unpipelined register-blocked kernel (A/B comparison)
+static int g_ts3_rows = 32;        // tile rows of the pipelined kernel at r = 16
+
+// Shared memory of the pipelined pass for the given arguments, or 0 if it does not apply.
+static size_t ts3_plan(const TSArgs &a, int *tr) {
+  if (g_force_ts2 || g_force_v1 || a.apply_h) return 0;
+  if (a.mode == 0 && a.out) return 0;
+  const int r = a.r, nq = a.nq, gl = a.gram_left, mode = a.mode;
+  const int nb = nq + (mode != 2 ? 1 : 0);
+  if (nb < 1 || nb > 8 || gl + 1 > 8 || gl > nq || (mode == 2 && nq < 1)) return 0;
+  auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  for (int m = 0; m < nq; ++m)
+    if (!al(a.q[m])) return 0;
+  if (mode != 2 && !al(a.src)) return 0;
+  if (a.out && !al(a.out)) return 0;
+  size_t b = 0;
+  if (r == 16) {
+    *tr = g_ts3_rows;
+    b = g_ts3_rows == 32 ? ts3_bytes<16, 32>(nq, gl, mode) : ts3_bytes<16, 64>(nq, gl, mode);
+  } else if (r == 8) {
+    *tr = 64;
+    b = ts3_bytes<8, 64>(nq, gl, mode);
+  } else if (r == 32) {
+    *tr = 32;
+    b = ts3_bytes<32, 32>(nq, gl, mode);
+  } else {
+    return 0;
+  }
+  return b <= 227 * 1024 ? b : 0;
+}
+
+static int launch_ts3(const TSArgs &a, int nsm, cudaStream_t st, size_t bytes, int tr) {
+  const cx<float> *coefg = nullptr;
+  if (a.mode != 0) {
+    if (!a.coef_scratch) return -1;
+    coefg = reinterpret_cast<const cx<float> *>(a.coef_scratch);
+    ::lrei::count_launch();
+    coef_convert2_kernel<float><<<8, 256, 0, st>>>(a.coefQ, a.coefS, a.nq, a.r, a.mode,
+                                                  reinterpret_cast<cx<float> *>(a.coef_scratch));
+  }
+  // persistent, each CTA walking tiles blockIdx.x, + gridDim.x, ...: one CTA per SM at 64-row
+  // tiles, two at 32-row tiles (at most 128 registers per thread and 110 KB of shared memory)
+  const long long ntiles = (a.N + tr - 1) / tr;
+  const long long cap = (tr <= 32 && bytes <= 110 * 1024) ? 2LL * nsm : (long long)nsm;
+  int grid = (int)(ntiles < cap ? ntiles : cap);
+  if (grid < 1) grid = 1;
+  ::lrei::count_launch();
+  const int g = a.gram_left + 1;
+  if (a.r == 16 && tr == 32) {
+    if (g <= 2) ts3_kernel<16, 32, 2><<<grid, 256, bytes, st>>>(a, coefg);
+    else if (g <= 3) ts3_kernel<16, 32, 3><<<grid, 256, bytes, st>>>(a, coefg);
+    else if (g <= 4) ts3_kernel<16, 32, 4><<<grid, 256, bytes, st>>>(a, coefg);
+    else if (g <= 5) ts3_kernel<16, 32, 5><<<grid, 256, bytes, st>>>(a, coefg);
+    else ts3_kernel<16, 32, 8><<<grid, 256, bytes, st>>>(a, coefg);
+  } else if (a.r == 16) {
+    if (g <= 2) ts3_kernel<16, 64, 2><<<grid, 256, bytes, st>>>(a, coefg);
+    else if (g <= 3) ts3_kernel<16, 64, 3><<<grid, 256, bytes, st>>>(a, coefg);
+    else if (g <= 4) ts3_kernel<16, 64, 4><<<grid, 256, bytes, st>>>(a, coefg);
+    else if (g <= 5) ts3_kernel<16, 64, 5><<<grid, 256, bytes, st>>>(a, coefg);
+    else ts3_kernel<16, 64, 8><<<grid, 256, bytes, st>>>(a, coefg);
+  } else if (a.r == 8) {
+    ts3_kernel<8, 64, 8><<<grid, 256, bytes, st>>>(a, coefg);
+  } else {
+    ts3_kernel<32, 32, 8><<<grid, 256, bytes, st>>>(a, coefg);
+  }
+  return grid;
+}
+
 template <typename T>
 static int launch_ts_t(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_t st) {
+  if (sizeof(T) == 4) {
+    int tr3 = 0;
+    const size_t b3 = ts3_plan(a, &tr3);
+    if (b3) return launch_ts3(a, nsm, st, b3, tr3);
+  }
   const int r = a.r, rp = ts2_rp(r);
   const int NMT = (a.gram_left + 1) * rp / TS2<T>::MI * (rp / TS2<T>::MJ);
   const int mt = NMT <= TS_THREADS ? 1 : (NMT <= 2 * TS_THREADS ? 2 : 0);
@@ -724,8 +1089,13 @@ void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long 
     const int grid = (int)(ntile * (r / sw));
     const size_t bytes = (size_t)TR * 32;
     ::lrei::count_launch();
-    if (fp64) hv2_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
-    else hv2_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
+    if (g_hv_v2) {
+      if (fp64) hv2_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
+      else hv2_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
+    } else {
+      if (fp64) hv3_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
+      else hv3_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
+    }
     return;
   }
   auto grid_for = [&](int cpt) {
@@ -897,12 +1267,31 @@ namespace lrei {
 // Raise the dynamic shared-memory limit of every tile kernel once (outside any stream capture).
 int ts_init() {
   g_force_v1 = getenv("LREI_TS_V1") != nullptr;
+  g_force_ts2 = getenv("LREI_TS2") != nullptr;
+  g_hv_v2 = getenv("LREI_HV2") != nullptr;
+  if (const char *e = getenv("LREI_TS3_ROWS")) g_ts3_rows = (atoi(e) == 64) ? 64 : 32;
   const int lim = 210 * 1024;
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {
     cudaError_t x = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (x != cudaSuccess) e = x;
   };
+  auto set3 = [&](const void *f) {
+    cudaError_t x = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (x != cudaSuccess) e = x;
+  };
+  set3((const void *)ts3_kernel<16, 64, 2>);
+  set3((const void *)ts3_kernel<16, 64, 3>);
+  set3((const void *)ts3_kernel<16, 64, 4>);
+  set3((const void *)ts3_kernel<16, 64, 5>);
+  set3((const void *)ts3_kernel<16, 64, 8>);
+  set3((const void *)ts3_kernel<16, 32, 2>);
+  set3((const void *)ts3_kernel<16, 32, 3>);
+  set3((const void *)ts3_kernel<16, 32, 4>);
+  set3((const void *)ts3_kernel<16, 32, 5>);
+  set3((const void *)ts3_kernel<16, 32, 8>);
+  set3((const void *)ts3_kernel<8, 64, 8>);
+  set3((const void *)ts3_kernel<32, 32, 8>);
   set((const void *)ts_kernel<double, 2>);
   set((const void *)ts_kernel<double, 1>);
   set((const void *)ts_kernel<float, 4>);
@@ -920,6 +1309,8 @@ int ts_init() {
   set((const void *)ts2_kernel<float, 1, 2>);
   set((const void *)hv2_kernel<double>);
   set((const void *)hv2_kernel<float>);
+  set((const void *)hv3_kernel<double>);
+  set((const void *)hv3_kernel<float>);
   set((const void *)obs_kernel<double>);
   set((const void *)obs_kernel<float>);
   return e == cudaSuccess ? 0 : -1;

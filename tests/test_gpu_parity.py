@@ -371,3 +371,21 @@ def test_householder_route_equals_projector_and_oracle(mdl, precision):
     Zr, Wr, _ = lr.rhs_factors(Vs, lam, Hs, 0.4, mdl)
     assert np.abs(W1.cpu().numpy() - Wr).max() < tol * sc
     assert np.abs(Z1.cpu().numpy() - Zr).max() < tol * sc
+
+
+# ------------------------------------------------------- tall-skinny Gram entry point
+
+@pytest.mark.parametrize("precision,m", [("fp64", 1), ("fp64", 5), ("mixed", 3), ("mixed", 5)])
+def test_gram_entry_point_matches_numpy(precision, m):
+    # P = [B_0..B_{m-1}]^* B_{m-1} over N = 2048 rows (32 tiles of 64 rows, more CTAs than tiles)
+    w = li.workload(2, n=11, r=8)
+    L = ctx_for(w, precision)
+    L.set_state(dev(w.V, precision), w.lam)
+    rng = np.random.default_rng(5)
+    B = [rng.standard_normal((1 << w.n, w.r)) + 1j * rng.standard_normal((1 << w.n, w.r)) for _ in range(m)]
+    Bd = [dev(b, precision) for b in B]
+    P = L.gram(Bd).cpu().numpy()
+    Bh = [b.cpu().numpy().astype(np.complex128) for b in Bd]     # the values the kernel read
+    ref = np.concatenate(Bh, axis=1).conj().T @ Bh[-1]
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    assert np.abs(P - ref).max() <= tol * np.abs(ref).max()
