@@ -356,7 +356,7 @@ def run_ours(args):
     gram_s = g0.elapsed_time(g1) / reps * 1e-3     # includes its small deterministic reduction
     gram_flops = 8.0 * 5 * r * r * N                # complex MACs x 8 real flops
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12       # SMs x FP32 lanes x 2 flops x max SM clock
-    roof = {"kernel": "ts2_kernel<float,4,1> (Gram [Q_0..Q_3, S]^* S, 5 complex64 blocks, N=2^20, r=16)",
+    roof = {"kernel": "ts3_kernel<16,32,5> (Gram [Q_0..Q_3, S]^* S, 5 complex64 blocks, N=2^20, r=16)",
             "bound": "alu", "achieved": round(gram_flops / gram_s / 1e12, 3), "peak": round(fp32_peak, 1),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz", "unit": "TFLOP/s",
             "frac": round(gram_flops / gram_s / 1e12 / fp32_peak, 4), "ms_per_launch": round(gram_s * 1e3, 4),
@@ -380,7 +380,7 @@ def run_ours(args):
     alg_bytes = 2 * N * r * 8
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / hv_s / 1e9
-    roof_hv = {"kernel": "hv2_kernel<float> (Y = H V, matrix-free, slab-major)", "bound": "hbm",
+    roof_hv = {"kernel": "hv3_kernel<float> (Y = H V, matrix-free, slab-major)", "bound": "hbm",
                "achieved": round(achieved, 1), "peak": peak,
                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800",
                "unit": "GB/s", "frac": round(achieved / peak, 4), "ms_per_launch": round(hv_s * 1e3, 4),
