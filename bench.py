@@ -297,9 +297,9 @@ def run_ours(args):
     if not args.no_learned:
         from paper_2508_21200_gb300 import controller as ctl
         tol = max(args.tol, 5e-6)
-        train_w = [li.workload(4, t, n=n, r=16, kappa=0.1) for t, n in ((1, 14), (2, 16), (3, 18))]
+        train_w = [li.workload(4, t, n=n, r=16, kappa=0.1) for t, n in ((1, 14), (2, 16), (3, 16), (4, 18), (5, 18))]
         t_tr = time.perf_counter()
-        Xtr, Ytr = ctl.generate(train_w, t_end=0.4, tols=(1e-4, 3e-5, 1e-5, 5e-6), precision="mixed")
+        Xtr, Ytr = ctl.generate(train_w, t_end=0.6, tols=(1e-4, 3e-5, 1e-5, 5e-6), precision="mixed")
         net, tr_loss = ctl.fit(Xtr, Ytr, iters=2000, lr=2e-3)
         t_tr = time.perf_counter() - t_tr
 

@@ -122,8 +122,9 @@ int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
 
 /* Advance to t_end with RK4 and an adaptive step: controller 0 = the plain
  * rule (spectral-drift estimate, step doubling as judge), 1 = the learned
- * controller (falls back to the plain rule when its prediction is judged
- * wrong).  tol bounds the relative local error per step; it is raised to the
+ * controller (its step ratio may undercut the plain rule's freely and exceed it
+ * by at most 25%; after a rejected step it chose, the plain rule takes over for
+ * 16 steps).  tol bounds the relative local error per step; it is raised to the
  * rounding floor of the context's precision (LREI_TOL_FLOOR_FP64,
  * LREI_TOL_FLOOR_MIXED), below which the step-doubling estimate is noise.
  * Returns LREI_ERR_STEP, with the state of the last accepted step kept, when

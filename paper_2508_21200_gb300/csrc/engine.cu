@@ -1307,7 +1307,9 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
       const double pred = std::exp((double)c->net_host[0]);
       if (std::isfinite(pred)) {
-        ratio = std::fmin(2.0, std::fmax(0.2, pred));   // growth capped at 2x per step
+        // trust region around the plain rule's ratio: the network may shrink the step freely
+        // and grow it at most 25% beyond the plain choice (and never more than 2x per step)
+        ratio = std::fmin(std::fmin(2.0, 1.25 * ratio), std::fmax(0.2, pred));
         net_chose_h = true;
       }
     }

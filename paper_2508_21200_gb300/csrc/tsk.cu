@@ -189,9 +189,9 @@ __global__ void __launch_bounds__(256) hv2_kernel(const __grid_constant__ ModelA
 // and partner rows outside the tile are L2 hits).  The tile is held as 16-byte chunks; the two
 // halves of a row swap places in every other group of four rows, so the 8 lanes of a
 // quarter-warp reading 8 aligned rows (or any XOR image of them, which is what a bit-flip
-// partner lookup reads) touch 8 distinct bank groups with 128-bit loads.  Bonds are taken four
-// at a time: the four partner loads (shared or global) are issued before their multiply-adds,
-// so up to four L2 round trips per row are in flight together.
+// partner lookup reads) touch 8 distinct bank groups with 128-bit loads.  Bonds are taken BATCH
+// at a time: their partner loads (shared or global) are issued before the multiply-adds, so up
+// to BATCH L2 round trips per row are in flight together.
 // A 32-byte slab row as two 16-byte chunks, read as real words of type T.
 struct Row32 {
   float4 v[2];
@@ -219,7 +219,7 @@ template <> __device__ __forceinline__ void row_set<double>(Row32 &x, const doub
                        __int_as_float(__double2loint(w[3])), __int_as_float(__double2hiint(w[3])));
 }
 
-template <typename T>
+template <typename T, int BATCH>
 __global__ void __launch_bounds__(256) hv3_kernel(const __grid_constant__ ModelArgs M, const cx<T> *__restrict__ X,
                                                   cx<T> *__restrict__ Y, long long N, int r, int tbits) {
   constexpr int SW = 32 / sizeof(cx<T>);   // complex elements per slab row
@@ -242,11 +242,11 @@ __global__ void __launch_bounds__(256) hv3_kernel(const __grid_constant__ ModelA
     T acc[NW];
 #pragma unroll
     for (int q = 0; q < NW; ++q) acc[q] = (T)0;
-    for (int k0 = 0; k0 < M.nb; k0 += 4) {
-      Row32 p[4];
-      T jj[4];
+    for (int k0 = 0; k0 < M.nb; k0 += BATCH) {
+      Row32 p[BATCH];
+      T jj[BATCH];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < BATCH; ++u) {
         const int k = k0 + u;
         jj[u] = (T)0;
         p[u].v[0] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) hv3_kernel(const __grid_constant__ ModelA
         }
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < BATCH; ++u)
 #pragma unroll
         for (int q = 0; q < NW; ++q) acc[q] = fma(jj[u], row_word<T>(p[u], q), acc[q]);
     }
@@ -1093,8 +1093,9 @@ void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long 
       if (fp64) hv2_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
       else hv2_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
     } else {
-      if (fp64) hv3_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
-      else hv3_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
+      // four bonds per batch: eight measured 10% slower (register pressure)
+      if (fp64) hv3_kernel<double, 4><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
+      else hv3_kernel<float, 4><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
     }
     return;
   }
@@ -1309,8 +1310,8 @@ int ts_init() {
   set((const void *)ts2_kernel<float, 1, 2>);
   set((const void *)hv2_kernel<double>);
   set((const void *)hv2_kernel<float>);
-  set((const void *)hv3_kernel<double>);
-  set((const void *)hv3_kernel<float>);
+  set((const void *)hv3_kernel<double, 4>);
+  set((const void *)hv3_kernel<float, 4>);
   set((const void *)obs_kernel<double>);
   set((const void *)obs_kernel<float>);
   return e == cudaSuccess ? 0 : -1;
