@@ -789,7 +789,7 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
       a.src = qblock(c, l);
       a.apply_h = 1;
     } else {
-      launch_hv(c->fp64, c->M, qblock(c, l), c->Sbuf, c->N, r, c->nsm, st);
+      launch_hv(c->fp64, c->M, qblock(c, l), c->Sbuf, c->N, r, c->nsm, st, c->status_dev);
       a.src = c->Sbuf;
       a.apply_h = 0;
     }
@@ -989,7 +989,7 @@ void *ab_take(lrei_ctx *c) {
 int ab_push_current(lrei_ctx *c) {
   void *vk = ab_take(c), *yk = ab_take(c);
   LREI_CUDA_TRY(cudaMemcpyAsync(vk, c->V, (size_t)c->N * c->r * c->elem, cudaMemcpyDeviceToDevice, c->st));
-  launch_hv(c->fp64, c->M, c->V, yk, c->N, c->r, c->nsm, c->st);
+  launch_hv(c->fp64, c->M, c->V, yk, c->N, c->r, c->nsm, c->st, c->status_dev);
   c->ab_hist.insert(c->ab_hist.begin(), {vk, yk});
   return LREI_OK;
 }
@@ -1063,7 +1063,7 @@ int enqueue_ab_step(lrei_ctx *c, int m) {
   for (int i = 1; i < nb; ++i) {
     int rc;
     if (i == 1 && !c->fused_hv) {
-      launch_hv(c->fp64, c->M, c->V, yk, c->N, r, c->nsm, st);
+      launch_hv(c->fp64, c->M, c->V, yk, c->N, r, c->nsm, st, c->status_dev);
       rc = orth_block(c, 1, yk, 0, nullptr, qb, c->Rraw);
     } else {
       rc = (i == 1) ? orth_block(c, 1, c->V, 1, yk, qb, c->Rraw) : orth_block(c, i, raw[i], 0, nullptr, qb, c->Rraw);
@@ -1684,7 +1684,7 @@ int lrei_observables(lrei_ctx *c, lrei_obs *out) {
 int lrei_apply_h(lrei_ctx *c, const void *V_dev, void *Y_dev, int r) {
   if (!c || !V_dev || !Y_dev || V_dev == Y_dev || r < 1 || r > MAX_R) return LREI_ERR_ARG;
   enter(c);
-  launch_hv(c->fp64, c->M, V_dev, Y_dev, c->N, r, c->nsm, c->st);
+  launch_hv(c->fp64, c->M, V_dev, Y_dev, c->N, r, c->nsm, c->st, c->status_dev);
   leave(c);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? LREI_OK : cuda_fail(e, "apply_h");

@@ -16,6 +16,9 @@
 // (complex64 path, TwoSum), written out as FP64 partials.
 #include "tsk.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdlib>
 
 namespace lrei {
@@ -287,6 +290,151 @@ __global__ void __launch_bounds__(256) hv3_kernel(const __grid_constant__ ModelA
   }
 }
 
+// ------------------------------------------------ H.V, slab tiles staged by TMA
+// Same tiles and bond handling as hv3_kernel, but no thread loads global memory: the tile of
+// 2^tbits rows of the CTA's 32-byte column slab and every partner tile a bond reaches outside
+// it (the tile t0 ^ (mask & ~(TR - 1)), rows permuted by the mask's low bits) are copied into
+// shared memory by the tensor-memory accelerator (2-D boxes of 256 rows x 32 bytes), so the
+// gathers run as bulk copies instead of per-lane 32-byte requests.  Partner tiles stream
+// through two buffers: while the threads add one, the next is in flight.  A bond whose two
+// bits both lie above the tile is active for all rows of the tile or for none, so only active
+// ones are fetched.  CTAs go tile by tile (all slabs of a tile, then the next tile), so whole
+// 128-byte lines of the block are in use together.  Every wait on a copy is bounded; a wait
+// that runs out sets ST_TIMEOUT and the kernel finishes without using that buffer.
+__device__ __forceinline__ uint32_t hv5_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool hv5_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+
+// Row lr of a dense [TR][32 B] buffer; the two 16-byte halves are read in an order that
+// depends on bit 2 of the row, so a quarter-warp reading 8 rows of an aligned group (or an XOR
+// image of one) touches 8 distinct bank groups.
+__device__ __forceinline__ Row32 hv5_row(const float4 *buf, uint32_t lr) {
+  const uint32_t s = (lr >> 2) & 1u;
+  const float4 a = buf[2 * lr + s], b = buf[2 * lr + (s ^ 1u)];
+  Row32 o;
+  o.v[0] = s ? b : a;
+  o.v[1] = s ? a : b;
+  return o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtensorMap tmx,
+                                                  const __grid_constant__ ModelArgs M, cx<T> *__restrict__ Y,
+                                                  long long N, int r, int tbits, int *status) {
+  constexpr int NW = 32 / sizeof(T);
+  constexpr int RPT = 4;                      // rows per thread: TR = 1024 = 4 x 256
+  extern __shared__ __align__(1024) float4 hv5_buf[];   // [3][TR][2]
+  __shared__ __align__(8) unsigned long long bar[3];
+  __shared__ int ext_k[MAX_BONDS];
+  __shared__ int n_ext;
+  const uint32_t TR = 1u << tbits;
+  const long long ntile = N >> tbits;
+  const int nslab = (int)(gridDim.x / ntile);
+  const int slab = (int)(blockIdx.x % nslab);
+  const uint32_t t0 = (uint32_t)((blockIdx.x / nslab) << tbits);
+  const int x0 = slab * 8;                    // first 4-byte word of the slab in a row
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int n = 0;
+    for (int k = 0; k < M.nb; ++k) {
+      const uint32_t hi = M.mask[k] & ~(TR - 1), lo = M.mask[k] & (TR - 1);
+      if (!hi) continue;
+      if (!lo && !(((t0 >> M.bi[k]) ^ (t0 >> M.bj[k])) & 1u)) continue;   // inactive on this tile
+      ext_k[n++] = k;
+    }
+    n_ext = n;
+    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hv5_smem_addr(&bar[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const int ne = n_ext;
+  auto issue = [&](int b, uint32_t row0) {   // one thread
+    const uint32_t ba = hv5_smem_addr(&bar[b]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ba), "r"(TR * 32u) : "memory");
+    for (uint32_t y = 0; y < TR; y += 256) {
+      const uint32_t dst = hv5_smem_addr(hv5_buf + (size_t)b * TR * 2 + (size_t)y * 2);
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
+              "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmx)), "r"(x0), "r"((int)(row0 + y)), "r"(ba)
+          : "memory");
+    }
+  };
+  if (tid == 0) {
+    issue(0, t0);
+    if (ne > 0) issue(1, t0 ^ (M.mask[ext_k[0]] & ~(TR - 1)));
+    if (ne > 1) issue(2, t0 ^ (M.mask[ext_k[1]] & ~(TR - 1)));
+  }
+  bool ok = hv5_wait(hv5_smem_addr(&bar[0]), 0);
+  const float4 *own = hv5_buf;
+  T acc[RPT][NW], diag[RPT];
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const uint32_t lr = tid + 256u * i, b = t0 + lr;
+    diag[i] = (T)(M.c0 + M.bz * (0.5 * M.n - (double)__popc(b)));
+#pragma unroll
+    for (int q = 0; q < NW; ++q) acc[i][q] = (T)0;
+    for (int k = 0; k < M.nb; ++k) {
+      if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
+        diag[i] -= (T)M.jz[k];
+        if (M.mask[k] < TR) {
+          const T j = (T)M.jxy[k];
+          const Row32 p = hv5_row(own, lr ^ M.mask[k]);
+#pragma unroll
+          for (int q = 0; q < NW; ++q) acc[i][q] = fma(j, row_word<T>(p, q), acc[i][q]);
+        }
+      }
+    }
+  }
+  for (int e = 0; e < ne; ++e) {
+    const int b = 1 + (e & 1);
+    const bool got = hv5_wait(hv5_smem_addr(&bar[b]), (uint32_t)((e >> 1) & 1));
+    ok = ok && got;
+    const int k = ext_k[e];
+    const uint32_t lo = M.mask[k] & (TR - 1);
+    const T j = (T)M.jxy[k];
+    const float4 *pb = hv5_buf + (size_t)b * TR * 2;
+    if (got) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const uint32_t lr = tid + 256u * i, bb = t0 + lr;
+        if (((bb >> M.bi[k]) ^ (bb >> M.bj[k])) & 1u) {
+          const Row32 p = hv5_row(pb, lr ^ lo);
+#pragma unroll
+          for (int q = 0; q < NW; ++q) acc[i][q] = fma(j, row_word<T>(p, q), acc[i][q]);
+        }
+      }
+    }
+    __syncthreads();   // every thread is done with buffer b
+    if (tid == 0 && e + 2 < ne) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(b, t0 ^ (M.mask[ext_k[e + 2]] & ~(TR - 1)));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RPT; ++i) {
+    const uint32_t lr = tid + 256u * i, b = t0 + lr;
+    const Row32 o0 = hv5_row(own, lr);
+    T ow[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) ow[q] = fma(diag[i], row_word<T>(o0, q), acc[i][q]);
+    Row32 o;
+    row_set<T>(o, ow);
+    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)b * r + slab * (32 / sizeof(cx<T>)));
+    dst[0] = o.v[0];
+    dst[1] = o.v[1];
+  }
+  if (!ok && tid == 0 && status) atomicOr(status, ST_TIMEOUT);
+}
+
 // ------------------------------------------------------ accumulation
 // Error-free sum: s + e == a + b exactly (Knuth TwoSum).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
@@ -321,6 +469,8 @@ template <> struct Acc<float> {
 constexpr int TS_THREADS = 256;
 static bool g_force_v1 = false;   // selects the unblocked kernel (A/B comparison)
 static bool g_hv_v2 = false;       // selects the unswizzled slab-major H.V kernel (A/B comparison)
+static bool g_hv_v3 = false;       // selects the slab kernel with per-lane partner loads (A/B comparison)
+static PFN_cuTensorMapEncodeTiled_v12000 g_tmap_encode = nullptr;   // driver entry point (TMA descriptors)
 
 
 template <typename T>
@@ -1080,7 +1230,38 @@ void launch_reduce(const double *partial, int nparts, int len_doubles, double *o
   reduce_kernel<<<(len_doubles + 255) / 256, 256, 0, st>>>(tmp, nslice, len_doubles, out);
 }
 
-void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st) {
+// Tensor map of an N x r block viewed as N rows of (2 or 4) r 4-byte words, box 256 rows x 8 words.
+static bool hv5_tensor_map(CUtensorMap *tm, bool fp64, const void *X, long long N, int r) {
+  if (!g_tmap_encode) return false;
+  const cuuint64_t words = (cuuint64_t)r * (fp64 ? 4 : 2);
+  const cuuint64_t dims[2] = {words, (cuuint64_t)N};
+  const cuuint64_t strides[1] = {words * 4};
+  const cuuint32_t box[2] = {8, 256};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult rc = g_tmap_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(X), dims, strides, box, estr,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return rc == CUDA_SUCCESS;
+}
+
+void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
+               int *status) {
+  const size_t rowb = (size_t)r * (fp64 ? 16 : 8);
+  // TMA-staged tiles of 1024 rows x 32 bytes (three 32 KB buffers: two CTAs per SM)
+  if (!g_hv_v2 && !g_hv_v3 && !g_force_v1 && M.n >= 10 && rowb % 32 == 0 &&
+      (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+    CUtensorMap tm;
+    if (hv5_tensor_map(&tm, fp64, X, N, r)) {
+      const int tbits = 10;
+      const long long ntile = N >> tbits;
+      const int grid = (int)(ntile * (long long)(rowb / 32));
+      const size_t bytes = 3 * ((size_t)1 << tbits) * 32;
+      ::lrei::count_launch();
+      if (fp64) hv5_kernel<double><<<grid, 256, bytes, st>>>(tm, M, (cx<double> *)Y, N, r, tbits, status);
+      else hv5_kernel<float><<<grid, 256, bytes, st>>>(tm, M, (cx<float> *)Y, N, r, tbits, status);
+      return;
+    }
+  }
   const int sw = fp64 ? 2 : 4;
   if (r % sw == 0 && !g_force_v1) {
     int tbits = M.n < 11 ? M.n : 11;
@@ -1270,6 +1451,15 @@ int ts_init() {
   g_force_v1 = getenv("LREI_TS_V1") != nullptr;
   g_force_ts2 = getenv("LREI_TS2") != nullptr;
   g_hv_v2 = getenv("LREI_HV2") != nullptr;
+  g_hv_v3 = getenv("LREI_HV3") != nullptr;
+  {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_tmap_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  }
   if (const char *e = getenv("LREI_TS3_ROWS")) g_ts3_rows = (atoi(e) == 64) ? 64 : 32;
   const int lim = 210 * 1024;
   cudaError_t e = cudaSuccess;
@@ -1310,6 +1500,8 @@ int ts_init() {
   set((const void *)ts2_kernel<float, 1, 2>);
   set((const void *)hv2_kernel<double>);
   set((const void *)hv2_kernel<float>);
+  set((const void *)hv5_kernel<double>);
+  set((const void *)hv5_kernel<float>);
   set((const void *)hv3_kernel<double, 4>);
   set((const void *)hv3_kernel<float, 4>);
   set((const void *)obs_kernel<double>);

@@ -39,7 +39,8 @@ size_t ts_partial_doubles(int gram_left, int r);   // per CTA
 void launch_reduce(const double *partial, int nparts, int len_doubles, double *out, cudaStream_t st);
 
 // Y = H X (standalone matrix-free action), X, Y: N x r row-major of the given precision.
-void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st);
+void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
+               int *status = nullptr);
 
 // Observable Grams of V (N x r): blocks (column-major r x r each, complex double):
 //   0: V^*HV  1: (HV)^*(HV)  2: V^*V  3: V^* Mx V  4: V^* My V  5: V^* Mz V

@@ -61,14 +61,17 @@ def gpu_rho(L):
 # ------------------------------------------------------------------ H.V
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("n,r,cfg", [(3, 1, 1), (6, 3, 2), (9, 4, 1), (9, 16, 2), (10, 5, 2)])
+@pytest.mark.parametrize("n,r,cfg", [(3, 1, 1), (6, 3, 2), (9, 4, 1), (9, 16, 2), (10, 5, 2),
+                                     # n >= 10: more than one 1024-row tile, bonds astride and above
+                                     # the tiles, a periodic wrap (cfg 2)
+                                     (10, 4, 2), (11, 8, 2), (12, 16, 1), (12, 8, 2), (13, 4, 2)])
 def test_apply_h_matches_dense(precision, n, r, cfg):
     w = li.workload(cfg, n=n, r=r)
     L = ctx_for(w, precision, r_max=r)
     V = dev(w.V, precision)
     Y = torch.empty_like(V)
     L.apply_h(V, Y)
-    H = model.hamiltonian(n, w.bonds, w.B)
+    H = model.hamiltonian(n, w.bonds, w.B, sparse=n > 10)
     ref = H @ V.cpu().numpy().astype(np.complex128)
     err = np.abs(Y.cpu().numpy() - ref).max() / np.abs(ref).max()
     assert err < (1e-13 if precision == "fp64" else 2e-6), err
