@@ -326,21 +326,22 @@ __device__ __forceinline__ Row32 hv5_row(const float4 *buf, uint32_t lr) {
   return o;
 }
 
-template <typename T>
+template <typename T, int TB, int NBUF>
 __global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtensorMap tmx,
                                                   const __grid_constant__ ModelArgs M, cx<T> *__restrict__ Y,
                                                   long long N, int r, int tbits, int *status) {
   constexpr int NW = 32 / sizeof(T);
-  constexpr int RPT = 4;                      // rows per thread: TR = 1024 = 4 x 256
-  extern __shared__ __align__(1024) float4 hv5_buf[];   // [3][TR][2]
-  __shared__ __align__(8) unsigned long long bar[3];
+  constexpr int RPT = (1 << TB) / 256;        // rows per thread
+  extern __shared__ __align__(1024) float4 hv5_buf[];   // [1 + NBUF][TR][2]
+  __shared__ __align__(8) unsigned long long bar[1 + NBUF];
   __shared__ int ext_k[MAX_BONDS];
   __shared__ int n_ext;
-  const uint32_t TR = 1u << tbits;
-  const long long ntile = N >> tbits;
+  const uint32_t TR = 1u << TB;
+  (void)tbits;
+  const long long ntile = N >> TB;
   const int nslab = (int)(gridDim.x / ntile);
   const int slab = (int)(blockIdx.x % nslab);
-  const uint32_t t0 = (uint32_t)((blockIdx.x / nslab) << tbits);
+  const uint32_t t0 = (uint32_t)((blockIdx.x / nslab) << TB);
   const int x0 = slab * 8;                    // first 4-byte word of the slab in a row
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtens
       ext_k[n++] = k;
     }
     n_ext = n;
-    for (int i = 0; i < 3; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hv5_smem_addr(&bar[i])));
+    for (int i = 0; i < 1 + NBUF; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hv5_smem_addr(&bar[i])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
@@ -370,8 +371,7 @@ __global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtens
   };
   if (tid == 0) {
     issue(0, t0);
-    if (ne > 0) issue(1, t0 ^ (M.mask[ext_k[0]] & ~(TR - 1)));
-    if (ne > 1) issue(2, t0 ^ (M.mask[ext_k[1]] & ~(TR - 1)));
+    for (int e = 0; e < NBUF && e < ne; ++e) issue(1 + e, t0 ^ (M.mask[ext_k[e]] & ~(TR - 1)));
   }
   bool ok = hv5_wait(hv5_smem_addr(&bar[0]), 0);
   const float4 *own = hv5_buf;
@@ -395,8 +395,8 @@ __global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtens
     }
   }
   for (int e = 0; e < ne; ++e) {
-    const int b = 1 + (e & 1);
-    const bool got = hv5_wait(hv5_smem_addr(&bar[b]), (uint32_t)((e >> 1) & 1));
+    const int b = 1 + (e % NBUF);
+    const bool got = hv5_wait(hv5_smem_addr(&bar[b]), (uint32_t)((e / NBUF) & 1));
     ok = ok && got;
     const int k = ext_k[e];
     const uint32_t lo = M.mask[k] & (TR - 1);
@@ -414,9 +414,9 @@ __global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtens
       }
     }
     __syncthreads();   // every thread is done with buffer b
-    if (tid == 0 && e + 2 < ne) {
+    if (tid == 0 && e + NBUF < ne) {
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      issue(b, t0 ^ (M.mask[ext_k[e + 2]] & ~(TR - 1)));
+      issue(b, t0 ^ (M.mask[ext_k[e + NBUF]] & ~(TR - 1)));
     }
   }
 #pragma unroll
@@ -471,6 +471,7 @@ static bool g_force_v1 = false;   // selects the unblocked kernel (A/B compariso
 static bool g_hv_v2 = false;       // selects the unswizzled slab-major H.V kernel (A/B comparison)
 static bool g_hv_v3 = false;       // selects the slab kernel with per-lane partner loads (A/B comparison)
 static PFN_cuTensorMapEncodeTiled_v12000 g_tmap_encode = nullptr;   // driver entry point (TMA descriptors)
+static int g_hv5_cfg = 0;          // tile rows of the TMA H.V kernel: 0 = 256, 1 = 512, 2 = 1024 (A/B)
 
 
 template <typename T>
@@ -1247,18 +1248,26 @@ static bool hv5_tensor_map(CUtensorMap *tm, bool fp64, const void *X, long long 
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                int *status) {
   const size_t rowb = (size_t)r * (fp64 ? 16 : 8);
-  // TMA-staged tiles of 1024 rows x 32 bytes (three 32 KB buffers: two CTAs per SM)
+  // TMA-staged tiles of 32-byte row slabs: the CTA's own tile and two partner-tile buffers
   if (!g_hv_v2 && !g_hv_v3 && !g_force_v1 && M.n >= 10 && rowb % 32 == 0 &&
       (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
     CUtensorMap tm;
     if (hv5_tensor_map(&tm, fp64, X, N, r)) {
-      const int tbits = 10;
-      const long long ntile = N >> tbits;
-      const int grid = (int)(ntile * (long long)(rowb / 32));
-      const size_t bytes = 3 * ((size_t)1 << tbits) * 32;
-      ::lrei::count_launch();
-      if (fp64) hv5_kernel<double><<<grid, 256, bytes, st>>>(tm, M, (cx<double> *)Y, N, r, tbits, status);
-      else hv5_kernel<float><<<grid, 256, bytes, st>>>(tm, M, (cx<float> *)Y, N, r, tbits, status);
+      auto go = [&](auto kd, auto kf, int tb, int nbuf) {
+        const long long ntile = N >> tb;
+        const int grid = (int)(ntile * (long long)(rowb / 32));
+        const size_t bytes = (size_t)(1 + nbuf) * ((size_t)1 << tb) * 32;
+        ::lrei::count_launch();
+        if (fp64) kd<<<grid, 256, bytes, st>>>(tm, M, (cx<double> *)Y, N, r, tb, status);
+        else kf<<<grid, 256, bytes, st>>>(tm, M, (cx<float> *)Y, N, r, tb, status);
+      };
+      // 256-row tiles, two partner buffers (24 KB per CTA, up to 8 CTAs per SM): 0.231 ms at n=20,
+      // r=16; 512-row tiles 0.244 ms, 1024-row tiles 0.280 ms, four buffers no better
+      switch (g_hv5_cfg) {
+        case 1: go(hv5_kernel<double, 9, 2>, hv5_kernel<float, 9, 2>, 9, 2); break;
+        case 2: go(hv5_kernel<double, 10, 2>, hv5_kernel<float, 10, 2>, 10, 2); break;
+        default: go(hv5_kernel<double, 8, 2>, hv5_kernel<float, 8, 2>, 8, 2); break;
+      }
       return;
     }
   }
@@ -1452,6 +1461,7 @@ int ts_init() {
   g_force_ts2 = getenv("LREI_TS2") != nullptr;
   g_hv_v2 = getenv("LREI_HV2") != nullptr;
   g_hv_v3 = getenv("LREI_HV3") != nullptr;
+  if (const char *e = getenv("LREI_HV5_CFG")) g_hv5_cfg = atoi(e);
   {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -1500,8 +1510,12 @@ int ts_init() {
   set((const void *)ts2_kernel<float, 1, 2>);
   set((const void *)hv2_kernel<double>);
   set((const void *)hv2_kernel<float>);
-  set((const void *)hv5_kernel<double>);
-  set((const void *)hv5_kernel<float>);
+  set((const void *)hv5_kernel<double, 10, 2>);
+  set((const void *)hv5_kernel<float, 10, 2>);
+  set((const void *)hv5_kernel<double, 9, 2>);
+  set((const void *)hv5_kernel<float, 9, 2>);
+  set((const void *)hv5_kernel<double, 8, 2>);
+  set((const void *)hv5_kernel<float, 8, 2>);
   set((const void *)hv3_kernel<double, 4>);
   set((const void *)hv3_kernel<float, 4>);
   set((const void *)obs_kernel<double>);
