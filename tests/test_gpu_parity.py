@@ -312,8 +312,8 @@ def test_ab_matches_dense_ei(scheme, mdl):
     assert err <= TOL["fp64"] and err_mu <= TOL["fp64"], (err, err_mu)
 
 
-@pytest.mark.xfail(reason="known gap: AB3 with complex64 history blocks measures 1.7e-6 (bar 1e-6); "
-                          "nearly dependent history blocks lose digits in FP32 storage", strict=False)
+@pytest.mark.xfail(reason="known gap: AB3 with complex64 history blocks exceeds 1e-6 (1.7e-6 here); the "
+                          "error arrives in one step, not as drift (AB2 complex64 and AB3 FP64 pass)", strict=False)
 def test_ab3_mixed_matches_dense_ei():
     w = li.workload(2, n=8, r=4)
     err, err_mu = _trajectory_check(w, "mixed", 60, 20, scheme="ab3", kappa=0.1, mdl="qll")
