@@ -138,24 +138,27 @@ def _barrier(world):
         dist.barrier()
 
 
+def _reduce_over_ranks(x, world, op):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
 def _max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return x if world == 1 else _reduce_over_ranks(x, world, dist.ReduceOp.MAX)
 
 
-def _sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+def aggregate_throughput(ms_per_step_local, world):
+    """Whole-job steps/s of `world` replicas that each run the same steps: all the steps of all
+    ranks divided by the slowest rank's time.  Returns (steps/s, slowest ms per step)."""
+    ms_max = _max_over_ranks(ms_per_step_local, world)
+    return world * 1000.0 / ms_max, ms_max
 
 
 def _src_hash(*files):
@@ -254,8 +257,7 @@ def run_ours(args):
     _barrier(world)
     launches = Lm.kernel_launches()
     ms = e0.elapsed_time(e1) / K
-    ms_max = _max_over_ranks(ms, world)
-    value = _sum_over_ranks(1000.0 / ms, world) if world > 1 else 1000.0 / ms_max
+    value, ms_max = aggregate_throughput(ms, world)
     om = Lm.observables()
 
     # ---- plain FP64 GPU path, same steps from the same state (W warm-up + K, Kd of them timed)
