@@ -9,10 +9,15 @@
 // invariant subspace (sm_eig_topr), so only r x r Jacobi runs in FP64.
 #include "small.cuh"
 
+#include <cstdlib>
+
 namespace lrei {
 
 // [0] FP32 Jacobi calls, [1] FP32 sweeps, [2] FP64 Jacobi calls, [3] FP64 sweeps (diagnostics)
 __device__ unsigned long long g_jacobi_counters[4];
+
+// threads of the FP32 Jacobi CTA (1024; 512 selectable for comparison)
+static int g_jacobi_nt = 1024;
 
 __device__ __forceinline__ zd zdiv_real(zd a, double d) { return mk<double>(a.re / d, a.im / d); }
 __device__ __forceinline__ zd zdiv(zd a, zd d) {
@@ -226,8 +231,8 @@ struct Rot {
 };
 
 // One CTA.  A (k x k Hermitian, FP64 input) -> eigenpairs in working precision T.
-template <typename T>
-__global__ void __launch_bounds__(512) jacobi_kernel(const zd *__restrict__ Ain, int lda, int k, zd *__restrict__ Uout,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) jacobi_kernel(const zd *__restrict__ Ain, int lda, int k, zd *__restrict__ Uout,
                                                      int ldu, double *__restrict__ wout, cx<T> *Ug, int max_sweeps,
                                                      double tol, int *status, cx<float> *__restrict__ Uf, int nout) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -382,13 +387,18 @@ void sm_jacobi(bool fp64, const zd *A, int lda, int k, zd *U, int ldu, double *w
   if (fp64) {
     const bool in_smem = jacobi_smem<double>(k, true) <= lim;
     const size_t bytes = jacobi_smem<double>(k, in_smem);
-    ::lrei::count_launch(); jacobi_kernel<double><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<double> *)scratch,
+    ::lrei::count_launch(); jacobi_kernel<double, 512><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<double> *)scratch,
                                                  max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
   } else {
     const bool in_smem = jacobi_smem<float>(k, true) <= lim;
     const size_t bytes = jacobi_smem<float>(k, in_smem);
-    ::lrei::count_launch(); jacobi_kernel<float><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
-                                                max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
+    ::lrei::count_launch();
+    if (g_jacobi_nt == 512)
+      jacobi_kernel<float, 512><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
+                                                       max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
+    else
+      jacobi_kernel<float, 1024><<<1, 1024, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
+                                                         max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
   }
 }
 
@@ -661,8 +671,10 @@ namespace lrei {
 int sm_init() {
   const int lim = 210 * 1024;
   cudaFuncSetAttribute(trsv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaError_t a = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaError_t b = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaError_t a = cudaFuncSetAttribute(jacobi_kernel<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaError_t b = cudaFuncSetAttribute(jacobi_kernel<float, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(jacobi_kernel<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (const char *e = getenv("LREI_JACOBI_NT")) g_jacobi_nt = atoi(e) == 512 ? 512 : 1024;
   cudaError_t c = cudaFuncSetAttribute(newton_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess) ? 0 : -1;
 }
