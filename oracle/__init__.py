@@ -17,6 +17,9 @@ Modules:
                ARPACK partial eigensolver on the operator g (eq. g-func)
   exact     -- closed-form references: rank-one pure-state solution
                (eq. exact_q-LL, corrected reading) and the kappa=0 unitary flow
+  reduced   -- two-spin reduced density matrices R_kl (partial trace and the
+               paper's 16-expectation route) with concurrence and negativity
+               (Sec. 3.6)
   mlp       -- FP64 reference of the step-controller network (forward,
                backward, Adam) used to check the GPU training kernels
   controller-- the plain adaptive step/rank rules the GPU controller follows

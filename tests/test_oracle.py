@@ -392,3 +392,75 @@ def test_mlp_linear_limit_and_adam_first_step():
     mlp.adam_step(q, g, {}, lr=1e-2)
     for k in p:
         assert np.allclose(q[k] - p[k], -1e-2 * g[k] / (np.abs(g[k]) + 1e-8), atol=1e-15)
+
+
+# ------------------------------------------- two-spin reduced density matrices (Sec. 3.6)
+
+from oracle import reduced  # noqa: E402
+
+
+def _pure(psi):
+    psi = np.asarray(psi, dtype=np.complex128)
+    psi = psi / np.linalg.norm(psi)
+    return np.outer(psi, psi.conj()), psi[:, None], np.array([1.0])
+
+
+def test_bell_and_product_states_textbook_measures():
+    rho, _, _ = _pure([1, 0, 0, 1])                      # (|00> + |11>)/sqrt2
+    R = reduced.rdm_partial_trace(rho, 2, 0, 1)
+    assert np.allclose(R, rho)
+    assert abs(reduced.concurrence(R) - 1.0) < 1e-12 and abs(reduced.negativity(R) - 0.5) < 1e-12
+    rho, _, _ = _pure(np.kron([1, 1], [1, 2j]))          # a product state
+    R = reduced.rdm_partial_trace(rho, 2, 0, 1)
+    assert reduced.concurrence(R) < 1e-12 and reduced.negativity(R) < 1e-12
+
+
+@pytest.mark.parametrize("p", [0.0, 0.2, 1 / 3, 0.5, 0.8, 1.0])
+def test_werner_pair_closed_forms(p):
+    # p |Psi-><Psi-| + (1 - p) I/4: C = max(0, (3p - 1)/2), N = max(0, (3p - 1)/4)
+    psi = np.array([0, 1, -1, 0]) / np.sqrt(2)
+    R = p * np.outer(psi, psi) + (1 - p) * np.eye(4) / 4
+    assert abs(reduced.concurrence(R) - max(0.0, (3 * p - 1) / 2)) < 1e-12
+    assert abs(reduced.negativity(R) - max(0.0, (3 * p - 1) / 4)) < 1e-12
+
+
+def test_w_and_ghz_pairs():
+    w = np.zeros(8); w[[1, 2, 4]] = 1                      # W state of 3 spins
+    rho, _, _ = _pure(w)
+    for k, l in ((0, 1), (0, 2), (1, 2)):
+        R = reduced.rdm_partial_trace(rho, 3, k, l)
+        assert abs(reduced.concurrence(R) - 2 / 3) < 1e-12 and reduced.negativity(R) > 0.1
+    g = np.zeros(8); g[[0, 7]] = 1                         # GHZ: every pair is a classical mixture
+    rho, _, _ = _pure(g)
+    R = reduced.rdm_partial_trace(rho, 3, 0, 2)
+    assert np.allclose(R, np.diag([0.5, 0, 0, 0.5]))
+    assert reduced.concurrence(R) < 1e-12 and reduced.negativity(R) < 1e-12
+
+
+@pytest.mark.parametrize("k,l", [(0, 5), (2, 3), (4, 1)])
+def test_pauli_route_equals_partial_trace_on_low_rank_states(k, l):
+    n, r = 6, 3
+    rng = np.random.default_rng(11 + k)
+    V = np.linalg.qr(rng.standard_normal((1 << n, r)) + 1j * rng.standard_normal((1 << n, r)))[0]
+    lam = np.array([0.5, 0.3, 0.2])
+    rho = (V * lam) @ V.conj().T
+    R1 = reduced.rdm_partial_trace(rho, n, k, l)
+    R2 = reduced.rdm_pauli(V, lam, n, k, l)
+    assert np.abs(R1 - R2).max() < 1e-13
+    assert abs(np.trace(R1) - 1) < 1e-13 and np.allclose(R1, R1.conj().T, atol=1e-14)
+    assert np.linalg.eigvalsh(R1).min() > -1e-13
+    # swapping the sites swaps the factors of the basis
+    R3 = reduced.rdm_partial_trace(rho, n, l, k)
+    assert np.abs(R3 - R1.reshape(2, 2, 2, 2).transpose(1, 0, 3, 2).reshape(4, 4)).max() < 1e-13
+
+
+def test_planted_dropped_partial_transpose_is_caught(monkeypatch):
+    # plant the slip of forgetting the partial transpose in the oracle: the Bell pin fails
+    rho, _, _ = _pure([1, 0, 0, 1])
+    assert abs(reduced.negativity(rho) - 0.5) < 1e-12
+
+    def negativity_without_transpose(R):
+        w = np.linalg.eigvalsh(R)
+        return float(-np.sum(w[w < 0]))
+    monkeypatch.setattr(reduced, "negativity", negativity_without_transpose)
+    assert abs(reduced.negativity(rho) - 0.5) > 0.4
