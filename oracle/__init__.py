@@ -20,6 +20,8 @@ Modules:
   reduced   -- two-spin reduced density matrices R_kl (partial trace and the
                paper's 16-expectation route) with concurrence and negativity
                (Sec. 3.6)
+  werner    -- Werner-state initial data through the shifted low-rank
+               problem kappa -> (1-p) kappa (Sec. 5, eq. werner-sol)
   mlp       -- FP64 reference of the step-controller network (forward,
                backward, Adam) used to check the GPU training kernels
   controller-- the plain adaptive step/rank rules the GPU controller follows

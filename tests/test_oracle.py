@@ -464,3 +464,55 @@ def test_planted_dropped_partial_transpose_is_caught(monkeypatch):
         return float(-np.sum(w[w < 0]))
     monkeypatch.setattr(reduced, "negativity", negativity_without_transpose)
     assert abs(reduced.negativity(rho) - 0.5) > 0.4
+
+
+# ------------------------------------------------------ Werner-state initial data (Sec. 5)
+
+from oracle import werner  # noqa: E402
+
+
+
+@pytest.mark.parametrize("mdl", ["qll", "qllg"])
+@pytest.mark.parametrize("rank", [1, 2])
+def test_werner_shift_equals_full_rank_evolution(mdl, rank):
+    # the full-rank EI evolution of rho_W equals p I/N + (1 - p) rho_hat(t) with kappa -> (1-p) kappa
+    n, p, kappa, h, steps = 4, 0.3, 0.5, 0.01, 12
+    N = 1 << n
+    H = model.hamiltonian(n, li.chain_bonds(n, False), (0.0, 0.0, 0.5))
+    rng = np.random.default_rng(7 + rank)
+    if rank == 1:
+        ghz = np.zeros(N, dtype=np.complex128); ghz[[0, N - 1]] = 1 / np.sqrt(2)
+        V_hat, lam_hat = ghz[:, None], np.array([1.0])
+    else:
+        V_hat = np.linalg.qr(rng.standard_normal((N, 2)) + 1j * rng.standard_normal((N, 2)))[0]
+        lam_hat = np.array([0.7, 0.3])
+    rho_W = werner.werner_state(V_hat, lam_hat, p)
+    w, U = np.linalg.eigh(rho_W)
+    idx = np.argsort(-w, kind="stable")
+    V_full, lam_full = U[:, idx], w[idx]
+    V_full_t, _ = de.integrate(V_full, lam_full, H, kappa, mdl, h, steps, "rk4")
+    rho_full = de.state(V_full_t, lam_full)
+    V_hat_t = werner.evolve(V_hat, lam_hat, p, H, kappa, mdl, h, steps)
+    rho_shift = werner.werner_state(V_hat_t, lam_hat, p)
+    assert np.abs(rho_full - rho_shift).max() < 1e-12
+    # and the observable shortcut
+    Mz = model.magnetization_op("z", n)
+    assert abs(werner.expectation(H, V_hat_t, lam_hat, p) - np.trace(H @ rho_full)) < 1e-12
+    assert abs(werner.expectation(Mz, V_hat_t, lam_hat, p) - np.trace(Mz @ rho_full)) < 1e-12
+
+
+def test_planted_unshifted_kappa_is_caught():
+    # evolving rho_hat with the unshifted kappa misses the full-rank evolution
+    n, p, kappa, h, steps = 4, 0.3, 0.5, 0.01, 12
+    N = 1 << n
+    H = model.hamiltonian(n, li.chain_bonds(n, False), (0.0, 0.0, 0.5))
+    rng = np.random.default_rng(9)
+    V_hat = np.linalg.qr(rng.standard_normal((N, 2)) + 1j * rng.standard_normal((N, 2)))[0]
+    lam_hat = np.array([0.7, 0.3])
+    rho_W = werner.werner_state(V_hat, lam_hat, p)
+    w, U = np.linalg.eigh(rho_W)
+    idx = np.argsort(-w, kind="stable")
+    V_full_t, _ = de.integrate(U[:, idx], w[idx], H, kappa, "qll", h, steps, "rk4")
+    rho_full = de.state(V_full_t, w[idx])
+    V_bad, _ = de.integrate(V_hat, lam_hat, H, kappa, "qll", h, steps, "rk4")
+    assert np.abs(rho_full - werner.werner_state(V_bad, lam_hat, p)).max() > 1e-6
