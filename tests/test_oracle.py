@@ -516,3 +516,4 @@ def test_planted_unshifted_kappa_is_caught():
     rho_full = de.state(V_full_t, w[idx])
     V_bad, _ = de.integrate(V_hat, lam_hat, H, kappa, "qll", h, steps, "rk4")
     assert np.abs(rho_full - werner.werner_state(V_bad, lam_hat, p)).max() > 1e-6
+
