@@ -47,8 +47,9 @@ def magnetization_op(v: str, n: int, sparse: bool = False):
     return M / n
 
 
-def hamiltonian(n: int, bonds, B=(0.0, 0.0, 0.0), sparse: bool = False):
-    """Spin Hamiltonian of eq. H1 without DMI: sum over bonds of the XXZ exchange plus B . sum_i S_i."""
+def hamiltonian(n: int, bonds, B=(0.0, 0.0, 0.0), sparse: bool = False, dmi=None):
+    """Spin Hamiltonian of eq. H1: sum over bonds of the XXZ exchange, the Dzyaloshinskii-Moriya
+    term 2 d_ij . (S_i x S_j) when `dmi` (one 3-vector per bond) is given, plus B . sum_i S_i."""
     N = 1 << n
     H = sp.csr_matrix((N, N), dtype=np.complex128) if sparse else np.zeros((N, N), dtype=np.complex128)
     for b in range(len(bonds)):
@@ -57,6 +58,13 @@ def hamiltonian(n: int, bonds, B=(0.0, 0.0, 0.0), sparse: bool = False):
         for v, c in (("x", jxy), ("y", jxy), ("z", jz)):
             if c != 0.0:
                 H = H + 2.0 * c * (spin_op(v, i, n, sparse) @ spin_op(v, j, n, sparse))
+        if dmi is not None:
+            d = np.asarray(dmi[b], dtype=np.float64)
+            # (S_i x S_j)_x = S_i^y S_j^z - S_i^z S_j^y, and cyclically
+            for c, (u, w) in zip(d, (("y", "z"), ("z", "x"), ("x", "y"))):
+                if c != 0.0:
+                    H = H + 2.0 * c * (spin_op(u, i, n, sparse) @ spin_op(w, j, n, sparse)
+                                       - spin_op(w, i, n, sparse) @ spin_op(u, j, n, sparse))
     for v, c in zip("xyz", B):
         if c != 0.0:
             for i in range(n):

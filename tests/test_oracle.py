@@ -517,3 +517,41 @@ def test_planted_unshifted_kappa_is_caught():
     V_bad, _ = de.integrate(V_hat, lam_hat, H, kappa, "qll", h, steps, "rk4")
     assert np.abs(rho_full - werner.werner_state(V_bad, lam_hat, p)).max() > 1e-6
 
+
+
+# ------------------------------------------- Dzyaloshinskii-Moriya term of eq. H1 (NEXT-3)
+
+def test_two_spin_dmi_z_closed_form():
+    # 2J S1.S2 + 2D (S1 x S2)_z: triplet |uu>, |dd> at J/2; the Sz = 0 pair couples with
+    # amplitude J + iD, so its energies are -J/2 +- sqrt(J^2 + D^2)
+    J, D = 1.0, 0.4
+    bonds = li.Bonds(np.array([0]), np.array([1]), np.array([J]), np.array([J]))
+    H = model.hamiltonian(2, bonds, dmi=[(0.0, 0.0, D)])
+    w = np.sort(np.linalg.eigvalsh(H))
+    ref = np.sort([J / 2, J / 2, -J / 2 + np.hypot(J, D), -J / 2 - np.hypot(J, D)])
+    assert np.abs(w - ref).max() < 1e-13
+    assert abs(H[1, 2] - (J + 1j * D)) < 1e-14          # <ud|H|du>: bit 0 = up, site 0 = first factor
+
+
+def test_dmi_hermitian_antisymmetric_and_sz_conservation():
+    n = 4
+    bonds = li.chain_bonds(n, True)
+    rng = np.random.default_rng(5)
+    d = rng.standard_normal((len(bonds), 3))
+    H = model.hamiltonian(n, bonds, (0.1, 0.0, 0.5), dmi=d)
+    assert np.abs(H - H.conj().T).max() < 1e-14
+    # swapping the two sites of every bond flips the sign of its DM term
+    H0 = model.hamiltonian(n, bonds)
+    swapped = li.Bonds(bonds.site_j, bonds.site_i, bonds.jxy, bonds.jz)
+    Hs = model.hamiltonian(n, swapped, dmi=d)
+    assert np.abs((Hs - H0) + (model.hamiltonian(n, bonds, dmi=d) - H0)).max() < 1e-13
+    # a DM vector along z commutes with total S^z; one along x does not
+    Sz = sum(model.spin_op("z", i, n) for i in range(n))
+    dz = np.zeros_like(d); dz[:, 2] = d[:, 2]
+    Hz = model.hamiltonian(n, bonds, dmi=dz)
+    assert np.abs(Hz @ Sz - Sz @ Hz).max() < 1e-13
+    dx = np.zeros_like(d); dx[:, 0] = 1.0
+    Hx = model.hamiltonian(n, bonds, dmi=dx)
+    assert np.abs(Hx @ Sz - Sz @ Hx).max() > 1e-2
+    # sparse and dense builds agree
+    assert np.abs(model.hamiltonian(n, bonds, (0.1, 0.0, 0.5), sparse=True, dmi=d).toarray() - H).max() < 1e-14
