@@ -24,7 +24,6 @@ Modules:
                problem kappa -> (1-p) kappa (Sec. 5, eq. werner-sol)
   mlp       -- FP64 reference of the step-controller network (forward,
                backward, Adam) used to check the GPU training kernels
-  controller-- the plain adaptive step/rank rules the GPU controller follows
 
 Every function cites the passage it follows.
 """

@@ -17,7 +17,7 @@ Paper passages followed:
     projected stage matrices (Sec. 3.7)
   * Adams-Bashforth m-step form (Sec. 3.8), started with RK4 steps.
 
-Readings (listed in the design doc): AB2 uses b = (3/2, -1/2) (the printed -3/2 is
+Readings where the paper is ambiguous: AB2 uses b = (3/2, -1/2) (the printed -3/2 is
 a typo: the weights of a consistent 2-step AB method sum to one); the r
 largest eigenvalues are taken by algebraic value, matched in decreasing order
 to Lambda_0 sorted decreasingly.
@@ -131,6 +131,7 @@ def observables(V, lam0, H, Mops):
         out["m" + v] = float(np.real(np.trace(Mops[v] @ rho)))
     out["purity"] = float(np.real(np.trace(rho @ rho)))
     out["trace"] = float(np.real(np.trace(rho)))
+    out["comm_norm"] = float(np.linalg.norm(comm(rho, H)))      # ||[rho, H]||_F, dense
     return out
 
 

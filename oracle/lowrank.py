@@ -214,4 +214,14 @@ def observables(V, lam0, Hop, Mops):
     LS = lam0[:, None] * S
     out["purity"] = float(np.real(np.trace(LS @ LS)))
     out["trace"] = float(np.real(np.trace(LS)))
+    # [rho, H] = V Lambda (H V)^* - (H V) Lambda V^* = B J B^* with B = [V, H V] and
+    # J = [[0, Lambda], [-Lambda, 0]]; its Frobenius norm from the 2r x 2r Gram B^* B
+    HV = Hop @ V
+    Bm = np.hstack([V, HV])
+    r = V.shape[1]
+    J = np.zeros((2 * r, 2 * r), dtype=np.complex128)
+    J[:r, r:] = np.diag(lam0)
+    J[r:, :r] = -np.diag(lam0)
+    Gb = Bm.conj().T @ Bm
+    out["comm_norm"] = float(np.sqrt(max(np.real(np.trace(J @ Gb @ J.conj().T @ Gb)), 0.0)))
     return out

@@ -3,7 +3,7 @@
 Paper: Sec. 3.6 eq. spin_op (S_i^v as a Kronecker product with sigma_v/2 in
 factor i) and Sec. 5 eq. H1 (exchange + Zeeman Hamiltonian).  hbar = 1.
 
-Readings used here (each listed in the design doc):
+Readings used here (where the paper leaves a choice open):
   * the exchange sum of eq. H1 runs once over each listed bond (i, j); an
     XXZ bond carries 2*Jxy*(S^x S^x + S^y S^y) + 2*Jz*S^z S^z, which for
     Jxy = Jz = J is the paper's 2J S_i . S_j;

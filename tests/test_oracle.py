@@ -204,7 +204,8 @@ def test_rank1_closed_form_satisfies_qll():
 
 
 def test_printed_rank1_form_is_not_hermitian():
-    # The literal e^{-iH~t} rho0 e^{+iH~t} with H~ = (1 - i kappa) H is not Hermitian (reading in the design doc).
+    # The literal e^{-iH~t} rho0 e^{+iH~t} with H~ = (1 - i kappa) H is not Hermitian, so the
+    # oracle reads the closed form as psi(t) = exp(-(i + kappa) H t) psi0 / norm instead.
     import scipy.linalg as sla
     n, kappa, t = 4, 0.5, 0.7
     H = model.hamiltonian(n, li.chain_bonds(n, False), (0, 0, 0.5))
@@ -312,6 +313,56 @@ def test_lowrank_observables_match_dense():
     b = lr.observables(w.V, w.lam, Hs, Mo)
     for k in a:
         assert abs(a[k] - b[k]) < 1e-13
+
+
+def test_purity_equals_sum_of_squared_spectrum():
+    # Tr(rho^2) = sum_i lambda_i^2 for rho = V diag(lambda) V^* with orthonormal V (Sec. 3.6: the
+    # spectrum is conserved, so the purity is a function of Lambda_0 alone); also 1 for a pure state
+    n, r = 6, 4
+    w = li.workload(1, n=n, r=r)
+    H = model.hamiltonian(n, w.bonds, w.B)
+    Hs = model.hamiltonian(n, w.bonds, w.B, sparse=True)
+    Mo = {v: model.magnetization_op(v, n) for v in "xyz"}
+    for obs in (de.observables(w.V, w.lam, H, Mo), lr.observables(w.V, w.lam, Hs, Mo)):
+        assert abs(obs["purity"] - np.sum(w.lam ** 2)) < 1e-14
+        assert abs(obs["trace"] - 1.0) < 1e-14
+    psi = li.af1_state(n)[:, None]
+    assert abs(de.observables(psi, np.array([1.0]), H, Mo)["purity"] - 1.0) < 1e-15
+
+
+def test_commutator_norm_of_pure_state_is_twice_energy_variance():
+    # for rho = psi psi^*: ||[rho, H]||_F^2 = 2 (<H^2> - <H>^2); zero for an eigenvector of H
+    n = 6
+    rng = np.random.default_rng(5)
+    H = model.hamiltonian(n, li.chain_bonds(n, True), (0, 0, 0.3))
+    Hs = model.hamiltonian(n, li.chain_bonds(n, True), (0, 0, 0.3), sparse=True)
+    Mo = {v: model.magnetization_op(v, n) for v in "xyz"}
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi /= np.linalg.norm(psi)
+    e1 = np.vdot(psi, H @ psi).real
+    e2 = np.vdot(H @ psi, H @ psi).real
+    lam = np.array([1.0])
+    for obs in (de.observables(psi[:, None], lam, H, Mo), lr.observables(psi[:, None], lam, Hs, Mo)):
+        assert abs(obs["comm_norm"] ** 2 - 2.0 * (e2 - e1 * e1)) < 1e-12 * e2
+    w, U = np.linalg.eigh(H)
+    for obs in (de.observables(U[:, [3]], lam, H, Mo), lr.observables(U[:, [3]], lam, Hs, Mo)):
+        assert obs["comm_norm"] < 1e-12
+
+
+def test_planted_purity_and_commutator_mistakes_are_caught():
+    # the pins above fail for the plausible slips Tr(rho) in place of Tr(rho^2) and a commutator
+    # taken with the wrong sign of one term (rho H + H rho)
+    n, r = 5, 3
+    w = li.workload(1, n=n, r=r)
+    H = model.hamiltonian(n, w.bonds, w.B)
+    rho = de.state(w.V, w.lam)
+    assert abs(np.trace(rho).real - np.sum(w.lam ** 2)) > 1e-2
+    psi = li.af1_state(n) + li.af2_state(n)
+    psi /= np.linalg.norm(psi)
+    P = np.outer(psi, psi.conj())
+    e1 = np.vdot(psi, H @ psi).real
+    e2 = np.vdot(H @ psi, H @ psi).real
+    assert abs(np.linalg.norm(P @ H + H @ P) ** 2 - 2.0 * (e2 - e1 * e1)) > 1e-2
 
 
 # ---------------------------------------------- planted mistakes are caught
