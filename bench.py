@@ -14,7 +14,8 @@ replica of the workload ("replicas only": the method has no data-parallel
 exchange at this size) and value is the sum over ranks / max time.
 
 --impl reference times the CPU oracle (the paper-literal low-rank LREI:
-Householder complement + ARPACK on g) on the host cores, as a bounded sample.
+Householder complement + ARPACK on g) on the host cores: whole RK4 steps at the
+same size, all cores, then one step on one BLAS thread.
 """
 from __future__ import annotations
 
@@ -25,7 +26,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -44,84 +44,137 @@ def _peaks():
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi in loop mode (-lms) while the block runs: SM clock and throttle reasons."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, period_ms=100):
         self.gpu = gpu_index
+        self.period = period_ms
         self.samples = []
-        self._stop = threading.Event()
-        self._t = None
-
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
-                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
-                                     timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+        self._p = None
 
     def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
-        self._t.start()
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                        "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._p = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=10)
+        if self._p is None:
+            return
+        self._p.terminate()
+        try:
+            out = self._p.communicate(timeout=10)[0]
+        except Exception:
+            self._p.kill()
+            out = ""
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.samples.append(f)
 
     def summary(self):
-        if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(s[1]) for s in self.samples) if v is not None]
+        mx = [v for v in (num(s[2]) for s in self.samples) if v is not None]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
         for s in self.samples:
             for i, nm in enumerate(names):
-                if len(s) > 5 + i and s[5 + i].lower().startswith("active"):
+                if s[5 + i].lower().startswith("active"):
                     reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.samples)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ------------------------------------------------------------- CPU sample
-def cpu_sample(nsamples: int = 1):
-    """Time a bounded sample of the oracle's RK4 step at the benchmark size.
+# ------------------------------------------------------------- CPU oracle
+ORACLE_STEP = ("whole RK4 steps of the oracle's plain low-rank LREI (Householder complement, "
+               "ARPACK partial eigendecomposition of each stage, FP64) at n=20, r=16")
 
-    Sample = one right-hand-side evaluation (Householder complement) + one ARPACK
-    partial eigendecomposition of the first stage matrix; an RK4 step does four of
-    each (the later eigendecompositions have more terms, so 4x the sample
-    under-estimates the step time).  Returns seconds per RK4 step and the threads used.
-    """
-    import numpy as np
+
+def blas_threads():
+    """Threads of the BLAS library numpy loaded, asked from the library itself (None if unknown)."""
+    import ctypes
+    import numpy  # noqa: F401  (loads the BLAS library)
+    paths = set()
+    try:
+        for line in open("/proc/self/maps"):
+            path = line.split()[-1]
+            if "blas" in os.path.basename(path).lower() and ".so" in path:
+                paths.add(path)
+    except OSError:
+        return None
+    for path in sorted(paths):
+        try:
+            lib = ctypes.CDLL(path)
+        except OSError:
+            continue
+        for fn in ("scipy_openblas_get_num_threads64_", "scipy_openblas_get_num_threads",
+                   "openblas_get_num_threads64_", "openblas_get_num_threads", "mkl_get_max_threads"):
+            if hasattr(lib, fn):
+                f = getattr(lib, fn)
+                f.restype = ctypes.c_int
+                return int(f())
+    return None
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_steps(warmup, steps, budget_s):
+    """Time whole oracle RK4 steps at the benchmark size: `warmup` untimed steps, then up to
+    `steps` timed ones, stopping after the first step that ends past `budget_s` seconds."""
     import lrei_inputs as li
     from oracle import model, lowrank as lr
     w = li.workload(3)
     Hs = model.hamiltonian(w.n, w.bonds, w.B, sparse=True)
+    V = w.V
+    for _ in range(warmup):
+        V, _ = lr.lrei_rk_step(V, w.lam, Hs, w.kappa, w.model, w.dt, "rk4")
     times = []
-    for _ in range(nsamples):
+    t_start = time.perf_counter()
+    for _ in range(max(1, steps)):
         t0 = time.perf_counter()
-        Z, W, _ = lr.rhs_factors(w.V, w.lam, Hs, w.kappa, w.model)
-        terms = [(w.V * w.lam[None, :] + 0.5 * w.dt * Z, w.V, 0.5 * w.dt * W)]
-        lr.partial_eig(terms, 1 << w.n, w.r)
-        times.append(4.0 * (time.perf_counter() - t0))
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return times, threads
+        V, _ = lr.lrei_rk_step(V, w.lam, Hs, w.kappa, w.model, w.dt, "rk4")
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return {"seconds_per_step": times, "warmup": warmup, "blas_threads": blas_threads(),
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
-def run_cpu_sample_subprocess(nsamples=1):
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(nsamples)],
-                         capture_output=True, text=True, timeout=3600)
+def oracle_steps_subprocess(warmup, steps, budget_s, threads):
+    """oracle_steps in a fresh process whose BLAS uses `threads` threads (set before numpy loads)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-steps", str(steps),
+                          "--oracle-warmup", str(warmup), "--oracle-budget", str(budget_s)],
+                         capture_output=True, text=True, timeout=3600, env=env)
     for line in out.stdout.splitlines()[::-1]:
         if line.startswith("{"):
             return json.loads(line)
-    raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
+    raise RuntimeError("oracle timing failed: " + out.stderr[-2000:])
 
 
 # --------------------------------------------------------------- helpers
@@ -226,8 +279,8 @@ def run_ours(args):
     # CPU baseline first, in a separate process, before this process does heavy GPU work
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            cpu = run_cpu_sample_subprocess(1)
+        try:   # one whole oracle RK4 step on all host cores (about 10-60 s)
+            cpu = oracle_steps_subprocess(0, 1, 0.0, os.cpu_count() or 1)
         except Exception as e:  # report, never fake
             cpu = {"error": str(e)[:200]}
 
@@ -241,15 +294,23 @@ def run_ours(args):
         L.set_state(V, w.lam)
         return L
 
-    # ---- mixed path (headline)
+    # ---- mixed path (headline).  W warm-up steps; then, with the clock sampler running, untimed
+    # steps for about 1.5 s (so the sampler sees the GPU under this load) and the K timed steps
     Lm = make("mixed")
     Lm.step(w.dt, "rk4", W)
-    Lm.kernel_launches()
     torch.cuda.synchronize()
     _barrier(world)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        t_soak = time.perf_counter()
+        while time.perf_counter() - t_soak < 1.5:
+            Lm.step(w.dt, "rk4", 20)
+            torch.cuda.synchronize()
+        Lm.set_state(torch.from_numpy(w.V).to("cuda", torch.complex64), w.lam)
+        Lm.step(w.dt, "rk4", W)
+        Lm.kernel_launches()
         torch.cuda.synchronize()
+        _barrier(world)
         e0.record(stream)
         Lm.step(w.dt, "rk4", K)
         e1.record(stream)
@@ -280,16 +341,23 @@ def run_ours(args):
     err_mu = float(np.abs(om["ritz"] - od["ritz"]).max() / w.lam.max())
     del Ld
 
-    # ---- accuracy reference: the mixed path at dt/4 over the same span T = (W + K) dt (its own
-    # truncation error is 4^-4 of the dt path's; its rounding error is the mixed path's, ~1e-8)
-    T = (W + K) * w.dt
-    Lr = make("mixed")
-    Lr.step(w.dt / 4, "rk4", 4 * (W + K))
-    oref = Lr.observables()
-    del Lr
+    # ---- accuracy references: the mixed path at dt/4 over the span of the fixed-dt legs,
+    # (W + K) dt, and over the adaptive window [0, T] (its truncation error is 4^-4 of the dt
+    # path's; its rounding error is the mixed path's, ~1e-8)
+    def reference(span_steps):
+        Lr = make("mixed")
+        Lr.step(w.dt / 4, "rk4", 4 * span_steps)
+        o = Lr.observables()
+        del Lr
+        return o
 
-    def obs_err(o):
-        return max(abs(o[k] - oref[k]) / max(abs(oref[k]), s) for k, s in scales.items())
+    oref = reference(W + K)
+    T = args.t_adaptive
+    n_ad = int(round(T / w.dt))            # dt-equivalent steps of the adaptive window
+
+    def obs_err(o, ref=None):
+        ref = oref if ref is None else ref
+        return max(abs(o[k] - ref[k]) / max(abs(ref[k]), s) for k, s in scales.items())
 
     # ---- mixed precision + learned step controller (the headline): the network is trained
     # first on plain-controller data from smaller chains (GPU kernels), then the n=20 workload
@@ -304,6 +372,8 @@ def run_ours(args):
         Xtr, Ytr = ctl.generate(train_w, t_end=0.6, tols=(1e-4, 3e-5, 1e-5, 5e-6), precision="mixed")
         net, tr_loss = ctl.fit(Xtr, Ytr, iters=2000, lr=2e-3)
         t_tr = time.perf_counter() - t_tr
+
+        oref_ad = reference(n_ad)
 
         def adaptive(controller):
             L = make("mixed")
@@ -322,8 +392,8 @@ def run_ours(args):
             a1.record(stream)
             torch.cuda.synchronize()
             res = {"wall_ms": round(a0.elapsed_time(a1), 3), "controller_stats": L.controller_stats(),
-                   "obs_rel_err_vs_reference": obs_err(L.observables()), "gpu_launches": L.kernel_launches()}
-            res["equiv_steps_per_s"] = round((W + K) / (res["wall_ms"] * 1e-3), 3)
+                   "obs_rel_err_vs_reference": obs_err(L.observables(), oref_ad), "gpu_launches": L.kernel_launches()}
+            res["equiv_steps_per_s"] = round(n_ad / (res["wall_ms"] * 1e-3), 3)
             del L
             return res
         try:
@@ -382,7 +452,7 @@ def run_ours(args):
     alg_bytes = 2 * N * r * 8
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / hv_s / 1e9
-    roof_hv = {"kernel": "hv3_kernel<float> (Y = H V, matrix-free, slab-major)", "bound": "hbm",
+    roof_hv = {"kernel": "hv6_kernel<float,2> (Y = H V, matrix-free, full 128-byte rows, N=2^20, r=16)", "bound": "hbm",
                "achieved": round(achieved, 1), "peak": peak,
                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800",
                "unit": "GB/s", "frac": round(achieved / peak, 4), "ms_per_launch": round(hv_s * 1e3, 4),
@@ -412,14 +482,14 @@ def run_ours(args):
     if rank != 0:
         return
     head = value if learned is None else learned["equiv_steps_per_s"]
-    head_ms = ms_max if learned is None else learned["wall_ms"] / (W + K)
+    head_ms = ms_max if learned is None else learned["wall_ms"] / n_ad
     out = {"metric": METRIC, "value": round(head, 3), "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": round(head_ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64 bulk + f64 small solves", "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": "mixed_c64",
                       "controller": ("fixed dt" if learned is None else
-                                     "learned (value = dt=0.01-equivalent RK4 steps/s: (T/dt) / wall time of "
-                                     "the adaptive run from t=0 to T=(W+K) dt)"),
+                                     f"learned (value = dt=0.01-equivalent RK4 steps/s: (T/dt) / wall time of "
+                                     f"the adaptive run from t=0 to T={T:g})"),
                       "parallelism": f"replicas x{world}",
                       "l2": "inputs larger than L2: each N x r complex64 block is 134 MB and a step streams 5 of them"},
            "mixed_fixed_dt": {"steps_per_s": round(value, 3), "ms_per_step": round(ms_max, 4),
@@ -430,58 +500,61 @@ def run_ours(args):
            "speedup_vs_fp64": round((head / (1000.0 / ms_fp64)), 2),
            "learned": learned if learned_error is None else {"error": learned_error},
            "obs_rel_err_vs_fp64": err, "ritz_rel_err_vs_fp64": err_mu,
-           "roofline": roof, "roofline_hv": roof_hv, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+           "roofline": roof, "roofline_hv": roof_hv, "e2e": e2e, "gpu_launches": launches,
+           "clocks": dict(clk.summary(), window="1.5 s of untimed steps right before the timed steps, and the timed steps")}
     if cpu is not None:
         if "error" in cpu:
             out["cpu_baseline"] = {"error": cpu["error"]}
         else:
             sec = statistics.median(cpu["seconds_per_step"])
-            out["cpu_baseline"] = {"value": round(1.0 / sec, 6), "unit": "steps/s", "cores": cpu["threads"],
-                                   "kind": "oracle",
-                                   "sample": "1 RHS (Householder complement) + 1 ARPACK partial eig of stage 2 at "
-                                             "n=20 r=16, x4 per RK4 step (paper-literal low-rank CPU LREI, FP64)"}
+            out["cpu_baseline"] = {"value": round(1.0 / sec, 6), "unit": "steps/s",
+                                   "cores": cpu["blas_threads"] or cpu["nproc"], "kind": "oracle",
+                                   "cpu_model": cpu["cpu_model"], "nproc": cpu["nproc"],
+                                   "seconds_per_step": [round(x, 2) for x in cpu["seconds_per_step"]],
+                                   "sample": f"1 of the {ORACLE_STEP}, from the initial state, no warm-up; cores = "
+                                             "threads the BLAS library reports"}
     print(json.dumps(out))
 
 
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: whole RK4 steps at the benchmark size, all cores,
+    then one step on one BLAS thread.  Under torchrun only rank 0 runs it."""
     rank, world, _ = _dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
-    import lrei_inputs as li
-    from oracle import model, lowrank as lr
-    w = li.workload(3)
-    Hs = model.hamiltonian(w.n, w.bonds, w.B, sparse=True)
-    # warm-up: untimed, one ARPACK call (at most one, whatever W is: a sample takes tens of
-    # seconds on the host cores)
-    Z, Wm, _ = lr.rhs_factors(w.V, w.lam, Hs, w.kappa, w.model)
-    terms = [(w.V * w.lam[None, :] + 0.5 * w.dt * Z, w.V, 0.5 * w.dt * Wm)]
-    if args.warmup > 0:
-        lr.partial_eig(terms, 1 << w.n, w.r)
-    # timed: up to K samples, stopping once 150 s have been spent (at least one sample), so
-    # the run ends within a few minutes
-    times = []
-    t_start = time.perf_counter()
-    for _ in range(max(1, args.steps)):
-        t0 = time.perf_counter()
-        Z, Wm, _ = lr.rhs_factors(w.V, w.lam, Hs, w.kappa, w.model)
-        terms = [(w.V * w.lam[None, :] + 0.5 * w.dt * Z, w.V, 0.5 * w.dt * Wm)]
-        lr.partial_eig(terms, 1 << w.n, w.r)
-        times.append(4.0 * (time.perf_counter() - t0))
-        if time.perf_counter() - t_start > 150.0:
-            break
-    sec = sum(times) / len(times)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    sample = ("per step: 1 RHS (Householder complement) + 1 ARPACK partial eig of stage 2 at n=20 r=16, "
-              f"x4 (an RK4 step does 4 of each); {len(times)} of {max(1, args.steps)} samples timed "
-              "(150 s budget)")
+    nproc = os.cpu_count() or 1
+    t_run = time.perf_counter()
+    allc = oracle_steps_subprocess(min(args.warmup, 1), args.steps, args.ref_budget, nproc)
+    one = None
+    if not args.no_one_thread:
+        try:
+            one = oracle_steps_subprocess(0, 1, 0.0, 1)
+        except Exception as e:  # report, never fake
+            one = {"error": str(e)[:200]}
+    times = allc["seconds_per_step"]
+    sec = statistics.median(times)
     v = round(1.0 / sec, 6)
-    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 1),
-                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
-                      "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample},
-                      "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    cores = allc["blas_threads"] or nproc
+    sample = (f"{len(times)} timed {ORACLE_STEP} after {allc['warmup']} untimed; median; timed steps stop "
+              f"once {args.ref_budget:.0f} s have been spent")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
+            "steps": len(times), "warmup": allc["warmup"], "ms_per_step": round(sec * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": allc["cpu_model"], "nproc": allc["nproc"],
+                             "seconds_per_step": [round(x, 2) for x in times]},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": None}
+    if one is not None:
+        if "error" in one:
+            line["cpu_one_thread"] = one
+        else:
+            s1 = one["seconds_per_step"][0]
+            line["cpu_one_thread"] = {"value": round(1.0 / s1, 6), "unit": "steps/s", "seconds_per_step": round(s1, 2),
+                                      "blas_threads": one["blas_threads"], "sample": f"1 of the {ORACLE_STEP}"}
+    line["wall_s"] = round(time.perf_counter() - t_run, 1)
+    print(json.dumps(line))
 
 
 def main():
@@ -494,15 +567,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--t-adaptive", type=float, default=1.0, help="end of the adaptive window [0, T]")
     ap.add_argument("--judge-every", type=int, default=8)
-    ap.add_argument("--cpu-sample", type=int, default=0)
+    ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-warmup", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget", type=float, default=0.0, help=argparse.SUPPRESS)
+    ap.add_argument("--ref-budget", type=float, default=100.0,
+                    help="reference arm: stop the timed oracle steps after this many seconds")
+    ap.add_argument("--no-one-thread", action="store_true", help="reference arm: skip the 1-thread step")
     ap.add_argument("--kernels-only", action="store_true",
                     help="time only the roofline kernels (Gram pass, H.V) at chain size --n")
     ap.add_argument("--n", type=int, default=20)
     args = ap.parse_args()
-    if args.cpu_sample:
-        times, threads = cpu_sample(args.cpu_sample)
-        print(json.dumps({"seconds_per_step": times, "threads": threads}))
+    if args.oracle_steps:
+        print(json.dumps(oracle_steps(args.oracle_warmup, args.oracle_steps, args.oracle_budget)))
         return
     if args.kernels_only:
         run_kernels(args)

@@ -36,7 +36,7 @@ typedef struct lrei_ctx lrei_ctx; /* opaque; owns all device memory it uses */
 typedef enum {
   LREI_OK = 0,
   LREI_ERR_ARG = -1,         /* invalid argument (sizes, ranges, NULL) */
-  LREI_ERR_UNSUPPORTED = -2, /* valid physics outside this build (B_x, B_y != 0) */
+  LREI_ERR_UNSUPPORTED = -2, /* valid request outside this build (an AB basis wider than 160) */
   LREI_ERR_NONFINITE = -3,   /* NaN/Inf in an input or produced by a step */
   LREI_ERR_TRACE = -4,       /* Lambda not >= 0 or |sum(Lambda) - 1| > 1e-12 */
   LREI_ERR_RANK = -5,        /* V rank-deficient */
@@ -64,9 +64,10 @@ typedef enum {
 
 typedef enum { LREI_C128 = 0, LREI_C64 = 1 } lrei_dtype;
 
-/* Exchange bonds of the spin Hamiltonian, eq. H1 without DMI: each bond (i, j)
- * contributes 2*jxy*(S^x_i S^x_j + S^y_i S^y_j) + 2*jz*S^z_i S^z_j, i.e. a
- * pair-flip amplitude jxy and a diagonal +-jz/2.  Host arrays, copied. */
+/* Exchange bonds of the spin Hamiltonian, eq. H1: each bond (i, j) contributes
+ * 2*jxy*(S^x_i S^x_j + S^y_i S^y_j) + 2*jz*S^z_i S^z_j, i.e. a pair-flip amplitude jxy and a
+ * diagonal +-jz/2; a Dzyaloshinskii-Moriya term along z is added by lrei_set_dmi.  Host
+ * arrays, copied. */
 typedef struct {
   int nbonds;
   const int *site_i, *site_j;
@@ -78,8 +79,8 @@ typedef struct {
   double t;          /* simulated time */
   double energy;     /* Tr(rho H) */
   double mx, my, mz; /* Tr(rho M_v), M_v = (1/n) sum_i S_i^v */
-  double purity;     /* Tr((Lambda_0 V^*V)^2) of the stored factor */
-  double trace;      /* Tr(Lambda_0 V^*V) of the stored factor */
+  double purity;     /* Tr(rho^2): Tr((Lambda_0 V^*V)^2) of the stored factor (see lrei_set_werner) */
+  double trace;      /* Tr(rho): Tr(Lambda_0 V^*V) of the stored factor (see lrei_set_werner) */
   double orth_err;   /* max |V^*V - I| of the stored factor */
   double herm_err;   /* max |G - G^*| / max|G|, G = V^*HV */
   double comm_norm;  /* ||[rho, H]||_F */
@@ -90,8 +91,8 @@ typedef struct {
 
 /* Create a context for n spins (1 <= n <= 26).
  *   J       exchange bonds (eq. H1), site indices in [0, n)
- *   B       Zeeman field (B_x, B_y, B_z): H_Z = B . sum_i S_i; B_x = B_y = 0
- *           in this build (else LREI_ERR_UNSUPPORTED)
+ *   B       Zeeman field (B_x, B_y, B_z): H_Z = B . sum_i S_i (eq. H1's -mu b . S with the
+ *           field in energy units); B_x, B_y flip single spins
  *   lambda  damping kappa >= 0 of eqs. q-LL / q-LLG
  *   r_max   largest rank the context will hold (1..32)
  *   cuda_stream  cudaStream_t (may be NULL)
@@ -120,11 +121,15 @@ int lrei_get_state(lrei_ctx *ctx, void *V_dev_out, double *Lambda_host_out,
  * history across calls while scheme and dt stay the same. */
 int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
 
-/* Advance to t_end with RK4 and an adaptive step: controller 0 = the plain
- * rule (spectral-drift estimate, step doubling as judge), 1 = the learned
- * controller (its step ratio may undercut the plain rule's freely and exceed it
- * by at most 25%; after a rejected step it chose, the plain rule takes over for
- * 16 steps).  tol bounds the relative local error per step; it is raised to the
+/* Advance to t_end with RK4 and an adaptive step (the adaptive stepping Sec. 6 names as
+ * future work): controller 0 = the plain rule (local error = calibrated spectral drift of
+ * the unprojected rho_{k+1}, step doubling as judge every judge_every steps and after a
+ * rejection, h_new = h clip(0.9 (tol/err)^(1/5), 0.2, 5)); 1 = the learned controller (the
+ * attached network estimates the local error from the step's features, scaled by a factor
+ * refitted at every judge; judged every 4 judge_every steps, after a rejection, and when its
+ * estimate exceeds tol; a judge that finds the error more than 3x above the estimate hands
+ * control to the plain rule for 16 steps).  tol bounds the relative local
+ * error per step; it is raised to the
  * rounding floor of the context's precision (LREI_TOL_FLOOR_FP64,
  * LREI_TOL_FLOOR_MIXED), below which the step-doubling estimate is noise.
  * Returns LREI_ERR_STEP, with the state of the last accepted step kept, when
@@ -136,6 +141,25 @@ int lrei_step_adaptive(lrei_ctx *ctx, double t_end, double tol, int controller);
 
 /* Compute observables of the current state into a host struct (syncs). */
 int lrei_observables(lrei_ctx *ctx, lrei_obs *out);
+
+/* Dzyaloshinskii-Moriya vectors along z (eq. H1: 2 d_ij . (S_i x S_j) with d_ij = dz[b] e_z for
+ * bond b = (i, j) of lrei_create, in its order; d_ji = -d_ij).  The bond's flip part becomes
+ * (jxy + i dz) S^+_i S^-_j + (jxy - i dz) S^-_i S^+_j.  nbonds must equal the bond count given
+ * to lrei_create; dz = 0 everywhere restores the plain exchange.  Clears any multistep
+ * history; the stored state and t are kept. */
+int lrei_set_dmi(lrei_ctx *ctx, int nbonds, const double *dz);
+
+/* Werner-state initial data (Sec. 5, eq. werner-sol).  With weight p in [0, 1) the state is
+ * rho = p I/N + (1 - p) rho_hat, where rho_hat = V Lambda_0 V^* is the stored low-rank state.
+ * The q-LL and q-LLG flows keep that form, rho_hat following the same equation with the
+ * damping kappa replaced by (1 - p) kappa; so after this call every step uses (1 - p) kappa
+ * (kappa as given to lrei_create), and lrei_observables reports the observables of rho
+ * itself: energy, magnetisations and ||[rho, H]|| scaled by 1 - p (H and M_v are traceless),
+ * trace p + (1 - p) Tr rho_hat, purity p^2/N + 2 p (1 - p) Tr(rho_hat)/N + (1 - p)^2 Tr rho_hat^2,
+ * and ritz / lambda0 mapped to p/N + (1 - p) mu.  orth_err and herm_err stay those of the
+ * stored factor.  p = 0 restores the plain problem.  Clears any multistep history; the
+ * stored state and t are kept.  p outside [0, 1) or not finite returns LREI_ERR_ARG. */
+int lrei_set_werner(lrei_ctx *ctx, double p);
 
 /* Free the context and all device memory it owns. */
 int lrei_destroy(lrei_ctx *ctx);
@@ -176,6 +200,50 @@ int lrei_rhs(lrei_ctx *ctx, void *Z_dev, void *W_dev, double *G_host,
  * Requires r < N. */
 int lrei_householder(lrei_ctx *ctx, void *U_dev, double *T_host, double *D_host);
 
+/* Two-spin reduced density matrices (Sec. 3.6): for each pair (site_k[q], site_l[q]), k != l,
+ * R_kl = Tr over every other spin of rho, the 4 x 4 matrix in the basis |s_k s_l> (index
+ * 2 s_k + s_l, site k the first factor, s = 0 spin up), written to R_host + 32 q as complex
+ * column-major (element (i, j) at 2 (4 j + i)); and, from R_kl in FP64, the concurrence
+ * max(0, s1 - s2 - s3 - s4) (s_i the decreasing square roots of the eigenvalues of R Rt,
+ * Rt = (Y x Y) conj(R) (Y x Y); Wootters 1998) and the negativity (minus the sum of the
+ * negative eigenvalues of the partial transpose on spin l; Vidal and Werner 2002).  With a
+ * Werner weight p (lrei_set_werner) the results are those of p I/N + (1 - p) rho_hat, whose
+ * reduced matrix is p I/4 + (1 - p) R_hat.  Host arrays; R_host, concurrence_host and
+ * negativity_host may each be NULL.  1 <= npairs <= LREI_RDM_MAX_PAIRS; sites in [0, n).
+ * One pass over the factor per pair (plus one to orthonormalise it); syncs the stream. */
+#define LREI_RDM_MAX_PAIRS 4096
+int lrei_two_spin_rdm(lrei_ctx *ctx, int npairs, const int *site_k, const int *site_l, double *R_host,
+                      double *concurrence_host, double *negativity_host);
+
+/* Rank rule of the plain step/rank controller (the adaptive control Sec. 6 names as future
+ * work): drop the trailing eigenvalues of Lambda_0 (the smallest) while their cumulative weight
+ * w stays <= tol_r (at least one is kept), remove the matching columns of the factor, and
+ * renormalise the kept weights to trace one.  The state changes by ||rho - rho'||_1 <= 2 w, so
+ * every observable <A> moves by at most 2 w ||A||.  Lambda_0 is conserved by the q-LL and
+ * q-LLG flows (Sec. 3), so the rule gives the same answer at any time and one call suffices.
+ * Writes the new rank to *r_out and w to *dropped_out (either may be NULL).  Clears any
+ * multistep history.  tol_r < 0 or not finite returns LREI_ERR_ARG. */
+int lrei_truncate_rank(lrei_ctx *ctx, double tol_r, int *r_out, double *dropped_out);
+
+/* Checkpoint and resume.  lrei_checkpoint_save writes into host memory everything the next steps
+ * read, as stored: the factor V (not re-orthonormalised), Lambda_0, the last Ritz values, the
+ * leading r x r blocks of the measured Gram V^*V and of its Cholesky factor, t, the Werner
+ * weight, the adaptive controller's step and calibration, and an Adams-Bashforth history (its
+ * (V_l, H V_l) pairs, scheme and dt).  lrei_checkpoint_load restores it into a context created
+ * with the same n, bonds, field, kappa, model and precision (and r_max >= r); the integration
+ * then continues bit for bit as in the saved context (all reductions have a fixed order).
+ * lrei_checkpoint_bytes gives the size (0 without a state); a smaller buffer, another layout or
+ * a mismatching context returns LREI_ERR_ARG.  Both sync. */
+long long lrei_checkpoint_bytes(lrei_ctx *ctx);
+int lrei_checkpoint_save(lrei_ctx *ctx, void *buf_host, long long bytes);
+int lrei_checkpoint_load(lrei_ctx *ctx, const void *buf_host, long long bytes);
+
+/* Sweep limit (1..100, default 30) of the FP64 Jacobi that finishes each partial
+ * eigendecomposition (the Rayleigh-Ritz on the top-r subspace).  A step whose small eigenproblem
+ * needs more sweeps, or whose eigenpair residual stays above its tolerance, returns
+ * LREI_ERR_EIG_NOCONV with status bit 2 or 32 set. */
+int lrei_set_eig_sweeps(lrei_ctx *ctx, int max_sweeps);
+
 /* Raw device status bits of the last step / set_state call (diagnostics):
  * 1 non-finite, 2 small eigensolver sweep limit, 4 rank-deficient factor,
  * 8 bounded wait ran out, 16 trace, 32 eigenpair residual above tolerance. */
@@ -190,23 +258,24 @@ int lrei_debug_counters(unsigned long long *out4);
 long long lrei_kernel_launches(lrei_ctx *ctx);
 
 /* ---- observables without device allocation ---------------------------- */
-/* For callers that cannot allocate device memory: hosts whose own allocator has reserved
- * all of it (a framework's caching pool, a fixed memory budget) and monitoring loops that
- * must not pay an allocation's latency or fragment the heap on every call.  Computes
- * the observables of rho = V diag(Lambda) V^* exactly as lrei_observables does for a
- * context holding the same factor, but without a context: n, J and B describe the
- * Hamiltonian as in lrei_create, V_dev is the N x r factor (row-major, ld = r, dtype
+/* For callers that cannot allocate device memory: hosts whose own allocator has reserved all of
+ * it (a framework's caching pool, a fixed memory budget) and monitoring loops that must not
+ * pay an allocation's latency or fragment the heap on every call.  Computes the observables of
+ * rho = V diag(Lambda) V^* exactly as lrei_observables does for a context holding the same
+ * factor, but without a context: n, J and B describe the Hamiltonian as in lrei_create (same
+ * argument checks and error codes), V_dev is the N x r factor (row-major, ld = r, dtype
  * LREI_C128 or LREI_C64), Lambda_host its r weights.  ritz and t are left zero.
  * The paper has no counterpart: this is a deployment variant of the observable pass.
- * Scratch memory is one static device array of about 3.8 MB inside this library, held
- * by every GPU that loads it until the process exits; nothing is allocated per call.
- * The first call on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  Every part of the array a
- * call reads is first written by that call, so no part of it has to start at zero.  All
- * calls share the array:
- * calls that overlap on the GPU (other streams, other threads) race and must be
- * serialised by the caller.  r > LREI_NOALLOC_MAX_R returns LREI_ERR_ARG.  Syncs the
- * stream. */
+ * Scratch memory is one static device array of about 3.8 MB inside this library; nothing is
+ * allocated per call.  The array is committed when the library's device code is loaded on a
+ * device, which happens at the first call on that device (CUDA loads modules lazily by
+ * default), so make the first call before the caller's own allocator reserves device memory,
+ * and before any stream capture; the array is then held until the process exits.  Each call
+ * looks the array's device address up with the device current (no caching across context
+ * resets).  Every part of the array a call reads is first written by that call, so no part
+ * of it has to start at zero.  All calls share the array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * r > LREI_NOALLOC_MAX_R returns LREI_ERR_ARG.  Syncs the stream. */
 #define LREI_NOALLOC_MAX_R 16
 int lrei_observables_noalloc(int n, const lrei_bonds *J, const double B[3], const void *V_dev, int r,
                              int dtype, const double *Lambda_host, void *cuda_stream, lrei_obs *out);
@@ -254,7 +323,8 @@ typedef struct {
  * attempted step (features, h, drift, judged error or -1, accepted); h0 > 0 sets the first step.
  * Resets the statistics and the record. */
 int lrei_controller_config(lrei_ctx *ctx, int judge_every, int record, double h0);
-/* Network used by lrei_step_adaptive(..., controller = 1); output 0 is log(h_next / h). */
+/* Network used by lrei_step_adaptive(..., controller = 1); output 0 is log(err / drift), the
+ * natural log of the step's local error over the spectral drift of the unprojected rho_{k+1}. */
 int lrei_controller_attach(lrei_ctx *ctx, lrei_mlp *net);
 int lrei_controller_stats(lrei_ctx *ctx, lrei_ctrl_stats *out);
 /* Copies up to max_rows rows of LREI_CTRL_NFEAT + 4 doubles; *n_rows = rows recorded. */

@@ -19,7 +19,7 @@ import dataclasses
 import numpy as np
 
 __all__ = [
-    "Bonds", "chain_bonds", "haar_orthonormal", "dirichlet_spectrum",
+    "Bonds", "chain_bonds", "triangular_bonds", "haar_orthonormal", "dirichlet_spectrum",
     "basis_state", "af1_state", "af2_state", "ghz_state", "w_state",
     "Workload", "workload", "rng_for",
 ]
@@ -51,6 +51,31 @@ def chain_bonds(n: int, periodic: bool, J: float = 1.0, aniso: np.ndarray | None
     if aniso is not None:
         jz = jz + np.asarray(aniso, dtype=np.float64)[:m]
     return Bonds(si, sj, jxy, jz)
+
+
+def triangular_bonds(lx: int, ly: int, periodic: bool = True, J: float = 1.0) -> Bonds:
+    """Nearest-neighbour bonds of an lx x ly triangular lattice (sites row by row, site = y lx + x):
+    each site bonds to its right, upper and upper-right neighbours (the three lattice directions);
+    with periodic boundaries the neighbours wrap around, duplicate pairs are listed once."""
+    pairs = []
+    seen = set()
+    for y in range(ly):
+        for x in range(lx):
+            i = y * lx + x
+            for dx, dy in ((1, 0), (0, 1), (1, 1)):
+                xx, yy = x + dx, y + dy
+                if periodic:
+                    xx, yy = xx % lx, yy % ly
+                elif xx >= lx or yy >= ly:
+                    continue
+                j = yy * lx + xx
+                key = (min(i, j), max(i, j))
+                if i != j and key not in seen:
+                    seen.add(key)
+                    pairs.append((i, j))
+    si = np.array([p[0] for p in pairs], dtype=np.int32)
+    sj = np.array([p[1] for p in pairs], dtype=np.int32)
+    return Bonds(si, sj, np.full(len(pairs), float(J)), np.full(len(pairs), float(J)))
 
 
 def haar_orthonormal(N: int, r: int, rng: np.random.Generator) -> np.ndarray:

@@ -77,6 +77,15 @@ def load_library(path: str | None = None):
         "lrei_step": (I, [P, D, I, I]),
         "lrei_step_adaptive": (I, [P, D, D, I]),
         "lrei_observables": (I, [P, ctypes.POINTER(Obs)]),
+        "lrei_set_werner": (I, [P, D]),
+        "lrei_set_dmi": (I, [P, I, ctypes.POINTER(D)]),
+        "lrei_set_eig_sweeps": (I, [P, I]),
+        "lrei_checkpoint_bytes": (L, [P]),
+        "lrei_checkpoint_save": (I, [P, P, L]),
+        "lrei_checkpoint_load": (I, [P, P, L]),
+        "lrei_truncate_rank": (I, [P, D, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "lrei_two_spin_rdm": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D),
+                                  ctypes.POINTER(D), ctypes.POINTER(D)]),
         "lrei_destroy": (I, [P]),
         "lrei_error_string": (ctypes.c_char_p, [I]),
         "lrei_apply_h": (I, [P, P, P, I]),
@@ -189,6 +198,56 @@ class Lrei:
 
     def step_adaptive(self, t_end, tol, controller=0):
         _check(self._lib.lrei_step_adaptive(self._h, float(t_end), float(tol), int(controller)))
+
+    def set_dmi(self, dz):
+        """Dzyaloshinskii-Moriya vectors d_ij = dz[b] e_z, one per bond in the bonds' order (eq. H1)."""
+        dz = np.ascontiguousarray(dz, dtype=np.float64)
+        self._dz = dz
+        _check(self._lib.lrei_set_dmi(self._h, len(dz), dz.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def checkpoint(self):
+        """The state as a bytes object (lrei_checkpoint_save)."""
+        nb = int(self._lib.lrei_checkpoint_bytes(self._h))
+        buf = ctypes.create_string_buffer(max(nb, 1))
+        _check(self._lib.lrei_checkpoint_save(self._h, buf, nb))
+        return buf.raw[:nb]
+
+    def restore(self, blob):
+        """Continue from a checkpoint taken with the same model and precision (lrei_checkpoint_load)."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.lrei_checkpoint_load(self._h, buf, len(blob)))
+        self.r = int(np.frombuffer(blob[:20], dtype=np.int32)[4])   # header: 8-byte tag, version, n, r
+
+    def set_eig_sweeps(self, max_sweeps):
+        _check(self._lib.lrei_set_eig_sweeps(self._h, int(max_sweeps)))
+
+    def set_werner(self, p):
+        """rho = p I/N + (1 - p) rho_hat: shifted damping for the steps, observables of rho (Sec. 5)."""
+        _check(self._lib.lrei_set_werner(self._h, float(p)))
+
+    def two_spin_rdm(self, pairs):
+        """R_kl (npairs x 4 x 4 complex), concurrence and negativity for site pairs [(k, l), ...]."""
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        k = np.ascontiguousarray(pairs[:, 0])
+        l = np.ascontiguousarray(pairs[:, 1])
+        npairs = pairs.shape[0]
+        R = np.zeros(32 * npairs)
+        conc = np.zeros(npairs)
+        neg = np.zeros(npairs)
+        pi = ctypes.POINTER(ctypes.c_int)
+        pd = ctypes.POINTER(ctypes.c_double)
+        _check(self._lib.lrei_two_spin_rdm(self._h, npairs, k.ctypes.data_as(pi), l.ctypes.data_as(pi),
+                                           R.ctypes.data_as(pd), conc.ctypes.data_as(pd), neg.ctypes.data_as(pd)),
+               self._h)
+        Rc = (R[0::2] + 1j * R[1::2]).reshape(npairs, 4, 4).transpose(0, 2, 1)   # column-major -> [q, i, j]
+        return Rc, conc, neg
+
+    def truncate_rank(self, tol_r):
+        """Drop trailing eigenvalues of total weight <= tol_r; returns (new rank, dropped weight)."""
+        k, wgt = ctypes.c_int(), ctypes.c_double()
+        _check(self._lib.lrei_truncate_rank(self._h, float(tol_r), ctypes.byref(k), ctypes.byref(wgt)), self._h)
+        self.r = k.value
+        return k.value, wgt.value
 
     def observables(self):
         o = Obs()

@@ -1,11 +1,11 @@
 """Training and evaluation of the learned step controller.
 
 Data: the plain adaptive controller run with a step-doubling judge on every step
-(`judge_every=1`, `record=True`) on open chains of n = 12..18 spins; each record holds
-the step features and the judged local error of the step actually taken.  The target
-is the step ratio the plain rule would choose from that measured error,
-log clip(0.9 (tol / err)^(1/5), 0.2, 5).  Training runs on the GPU through the
-network's own gradient and Adam kernels.
+(`judge_every=1`, `record=True`) on open chains; each record holds the step features, the
+spectral drift of the step and its judged local error.  The target is log(err / drift): the
+network learns how the free drift indicator relates to the local error, so that the library's
+learned rule can estimate the error of a step without the extra two half-steps of a judge.
+Training runs on the GPU through the network's own gradient and Adam kernels.
 """
 from __future__ import annotations
 
@@ -14,11 +14,7 @@ import numpy as np
 from . import Lrei, Mlp, NFEAT
 
 
-def target_from_error(err, tol):
-    return np.log(np.clip(0.9 * (tol / np.maximum(err, 1e-300)) ** 0.2, 0.2, 5.0))
-
-
-def generate(workloads, t_end=0.3, tols=(1e-7, 1e-9), precision="fp64", device_tensor=None):
+def generate(workloads, t_end=0.3, tols=(1e-7, 1e-9), precision="fp64"):
     """Run the plain controller with per-step judging; return (X, Y) training arrays."""
     import torch
     Xs, Ys = [], []
@@ -30,9 +26,10 @@ def generate(workloads, t_end=0.3, tols=(1e-7, 1e-9), precision="fp64", device_t
             L.controller_config(judge_every=1, record=True, h0=0.01)
             L.step_adaptive(t_end, tol, 0)
             rows = L.controller_records()
-            ok = rows[:, NFEAT + 2] > 0
+            drift, err = rows[:, NFEAT + 1], rows[:, NFEAT + 2]
+            ok = (err > 0) & (drift > 0)
             Xs.append(rows[ok, :NFEAT])
-            Ys.append(target_from_error(rows[ok, NFEAT + 2], tol)[:, None])
+            Ys.append(np.log(err[ok] / drift[ok])[:, None])
             L.close()
     return np.concatenate(Xs).astype(np.float32), np.concatenate(Ys).astype(np.float32)
 

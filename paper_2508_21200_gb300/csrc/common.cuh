@@ -46,20 +46,28 @@ constexpr int MAX_SPINS = 26;
 constexpr int MAX_R = 32;
 constexpr int MAXB = 12;          // most N x r blocks one tall-skinny kernel reads
 
-// The spin Hamiltonian of eq. H1 (no DMI, Zeeman along z) in the form the
-// kernels use: per bond the two bit positions, its flip amplitude jxy and
-// its S^zS^z coefficient jz.  diag(b) = c0 - sum_{antiparallel bonds} jz
-// + bz * (n/2 - popcount(b)), with c0 = sum_bonds jz / 2.
+// The spin Hamiltonian of eq. H1 in the form the kernels use.  Per bond (i, j): the two bit
+// positions (bi of site i, bj of site j), the pair-flip amplitude jxy, the S^zS^z coefficient jz
+// and the z component dz of the Dzyaloshinskii-Moriya vector: the bond's flip part is
+// (jxy + i dz) S^+_i S^-_j + (jxy - i dz) S^-_i S^+_j, so row b of H V takes the partner
+// b ^ mask with amplitude jxy + i dz when site i is up in b (bit 0) and jxy - i dz when it is
+// down.  diag(b) = c0 - sum_{antiparallel bonds} jz + bz (n/2 - popcount(b)), c0 = sum jz / 2.
+// A transverse field (bx, by) flips one spin: row b takes b ^ 2^q with amplitude
+// (bx - i by)/2 when bit q of b is 0 and (bx + i by)/2 when it is 1.  cplx != 0 when any dz,
+// bx or by is nonzero (complex amplitudes or one-bit partners).
 struct ModelArgs {
   int n;
   int nb;
+  int cplx;
   double c0;
   double bz;
+  double bx, by;
   uint32_t mask[MAX_BONDS];
   uint8_t bi[MAX_BONDS];
   uint8_t bj[MAX_BONDS];
   double jxy[MAX_BONDS];
   double jz[MAX_BONDS];
+  double dz[MAX_BONDS];
 };
 
 // Device status word bits (written by kernels, read by the host after a step).
@@ -82,6 +90,10 @@ enum : int {
 
 namespace lrei {
 int cuda_fail(cudaError_t e, const char *what);
+// Validates n, the bonds (an lrei_bonds, may be NULL) and the field by the argument rules of
+// lrei_create and fills M.
+// Returns LREI_OK or the lrei_status code.
+int build_model_args(int n, const void *bonds, const double B[3], ModelArgs *M);
 // Kernels launched (or recorded into a graph) by this library's wrappers in this process.
 long long launch_counter();
 void count_launch(int n = 1);

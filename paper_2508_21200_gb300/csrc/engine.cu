@@ -27,6 +27,11 @@
 #include "tsk.cuh"
 
 namespace lrei { int sm_read_counters(unsigned long long *out); }
+namespace lrei {
+int launch_rdm(bool fp64, const void *V, long long N, int r, const double *lam, const int *pairs, int npairs,
+               double *partial, int ncta, cudaStream_t st);
+void launch_rdm_final(const double *partial, int nparts, int npairs, double p_werner, double *out, cudaStream_t st);
+}  // namespace lrei
 // controller network inference on a given stream (mlp.cu)
 int lrei_mlp_forward_on(lrei_mlp *net, const float *X, int B, float *Y, cudaStream_t st);
 
@@ -180,15 +185,29 @@ __global__ void store_rc_kernel(const zd *__restrict__ Lr, int r, const int *__r
   }
 }
 
-// New rows k..k+r-1 of the Cholesky factor of Gamma: [Bs^H | L22], dead rows decoupled.
+// New rows k..k+r-1 of the Cholesky factor of Gamma: [Bs^H | L22].  A dead column (numerically
+// dependent on the earlier ones) is decoupled from the later columns; with keep_dead its row keeps
+// the projections onto the earlier frame vectors, else it is zeroed too.  dead_frame (may be NULL)
+// receives the dead flags of the new columns.
 __global__ void store_lrows_kernel(const zd *__restrict__ Bs, int ldb, const zd *__restrict__ L22, int r, int k,
-                                   const int *__restrict__ dead, zd *__restrict__ L, int ldl) {
+                                   const int *__restrict__ dead, zd *__restrict__ L, int ldl, int keep_dead,
+                                   int *__restrict__ dead_frame) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * (k + r); e += gridDim.x * blockDim.x) {
     const int j = e % r, m = e / r;   // row k + j, column m
     zd v;
-    if (m < k) v = dead[j] ? mk<double>(0, 0) : conj(Bs[(size_t)j * ldb + m]);
+    if (m < k) v = (dead[j] && !keep_dead) ? mk<double>(0, 0) : conj(Bs[(size_t)j * ldb + m]);
     else v = L22[(size_t)(m - k) * r + j];
     L[(size_t)m * ldl + (k + j)] = v;
+  }
+  if (dead_frame && blockIdx.x == 0)
+    for (int j = threadIdx.x; j < r; j += blockDim.x) dead_frame[k + j] = dead[j];
+}
+
+// Rows of A (M x N) whose frame column is dead are set to zero.
+__global__ void zero_dead_rows_kernel(zd *__restrict__ A, int lda, int M, int N, const int *__restrict__ dead_frame) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x) {
+    const int i = e % M, j = e / M;
+    if (dead_frame[i]) A[(size_t)j * lda + i] = mk<double>(0, 0);
   }
 }
 
@@ -233,8 +252,13 @@ __global__ void lhl_kernel(const zd *__restrict__ L, int r, const double *__rest
 // Observables from the Gram blocks of the observable pass (one CTA, r <= 32).
 // The stored factor V is orthonormalised implicitly: with V^*V = L L^H and X = L^{-1},
 // Tr(rho A) = Tr(Lambda X (V^*AV) X^H).
+// With Werner weight p (Sec. 5, eq. werner-sol) the state is rho = p I/N + (1 - p) rho_hat, rho_hat the
+// stored low-rank state: H and the magnetisations are traceless, so their expectations and [rho, H] scale
+// by q = 1 - p; Tr rho = p + q Tr rho_hat; Tr rho^2 = p^2/N + 2 p q Tr(rho_hat)/N + q^2 Tr rho_hat^2; each
+// eigenvalue mu of rho_hat becomes p/N + q mu.  When mu is given, out[16 + i] receives the mapped Ritz
+// values and out[48 + i] the mapped spectrum.
 __global__ void obs_final_kernel(const double *__restrict__ red, int r, const double *__restrict__ lam,
-                                 double *__restrict__ out) {
+                                 double *__restrict__ out, double p, double inv_n, const double *__restrict__ mu) {
   // blocks: 0 V^*HV, 1 (HV)^*(HV), 2 V^*V, 3 V^*MxV, 4 V^*MyV, 5 V^*MzV
   extern __shared__ zd s[];
   zd *Lg = s, *X = s + r * r, *T = s + 2 * r * r, *Ab = s + 3 * r * r;
@@ -317,16 +341,22 @@ __global__ void obs_final_kernel(const double *__restrict__ red, int r, const do
         gmax = fmax(gmax, sqrt(norm2(a)));
       }
     }
-    out[0] = tot[0];
-    out[1] = tot[2];
-    out[2] = tot[3];
-    out[3] = tot[4];
-    out[4] = purity;
-    out[5] = trace;
+    const double q = 1.0 - p;
+    out[0] = q * tot[0];
+    out[1] = q * tot[2];
+    out[2] = q * tot[3];
+    out[3] = q * tot[4];
+    out[4] = p * p * inv_n + 2.0 * p * q * inv_n * trace + q * q * purity;
+    out[5] = p + q * trace;
     out[6] = orth;
     out[7] = gmax > 0 ? herm / gmax : 0.0;
-    out[8] = sqrt(fmax(0.0, 2.0 * tot[1] - 2.0 * tot[5]));
+    out[8] = q * sqrt(fmax(0.0, 2.0 * tot[1] - 2.0 * tot[5]));
   }
+  if (mu)
+    for (int i = t; i < r; i += nt) {
+      out[16 + i] = p * inv_n + (1.0 - p) * mu[i];
+      out[48 + i] = p * inv_n + (1.0 - p) * lam[i];
+    }
 }
 
 // ----------------------------------------------------------- controller features
@@ -352,21 +382,40 @@ __global__ void feat_comm_kernel(const zd *__restrict__ T, int K, int ld, const 
 // (spectral drift of the unprojected rho_{k+1}).
 __global__ void feat_final_kernel(const double *__restrict__ mu, const double *__restrict__ lam, int r,
                                   const zd *__restrict__ G0, const zd *__restrict__ Gl, double *__restrict__ feat) {
-  if (threadIdx.x != 0) return;
-  double d = 0, n0 = 0, dr = 0, lm = 0;
-  for (int e = 0; e < r * r; ++e) {
+  // one entry per thread (FP64 issues slowly on this part: a one-thread loop over r^2 entries
+  // takes ~0.1 ms), then a block reduction
+  __shared__ double red[3][8];
+  const int t = threadIdx.x;
+  double d = 0, n0 = 0, dr = 0;
+  for (int e = t; e < r * r; e += blockDim.x) {
     const int i = e % r, j = e / r;
     const zd a = Gl[e], b = Gl[(size_t)i * r + j];
     const zd h = mk<double>(0.5 * (a.re + b.re), 0.5 * (a.im - b.im));
     d += norm2(h - G0[e]);
     n0 += norm2(G0[e]);
   }
-  for (int i = 0; i < r; ++i) {
+  double lm = 0;
+  for (int i = t; i < r; i += blockDim.x) {
     dr = fmax(dr, fabs(mu[i] - lam[i]));
     lm = fmax(lm, lam[i]);
   }
-  feat[1] = n0 > 0 ? sqrt(d / n0) : 0.0;
-  feat[2] = lm > 0 ? dr / lm : 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+    n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+    dr = fmax(dr, __shfl_xor_sync(0xffffffffu, dr, o));
+    lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+  }
+  __shared__ double lmax[8];
+  if ((t & 31) == 0) { red[0][t >> 5] = d; red[1][t >> 5] = n0; red[2][t >> 5] = dr; lmax[t >> 5] = lm; }
+  __syncthreads();
+  if (t == 0) {
+    double D = 0, N0 = 0, DR = 0, LM = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+      D += red[0][w]; N0 += red[1][w]; DR = fmax(DR, red[2][w]); LM = fmax(LM, lmax[w]);
+    }
+    feat[1] = N0 > 0 ? sqrt(D / N0) : 0.0;
+    feat[2] = LM > 0 ? DR / LM : 0.0;
+  }
 }
 
 // Frobenius distance between two states rho_a = Va La Va^*, rho_b (same spectrum Lambda), from
@@ -510,6 +559,15 @@ __global__ void dist_final_kernel(const zd *__restrict__ PP, int r, const double
   out[3] = sqrt(out[1]);
 }
 
+// ---------------------------------------------------------- rank truncation
+// dst (N x k, row-major) = the first k columns of src (N x r, row-major).
+template <typename T>
+__global__ void keep_cols_kernel(const cx<T> *__restrict__ src, int r, cx<T> *__restrict__ dst, int k, long long N) {
+  const long long total = N * k;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = src[(e / k) * r + e % k];
+}
+
 // ---------------------------------------------------------- Householder route
 // Compact-WY form Q = I - U T U^H of the r Householder reflectors that triangularise the
 // orthonormal factor V (Sec. 3.4, eq. Householder-mat), reconstructed from V itself: with
@@ -630,7 +688,7 @@ __global__ void x11_from_g_kernel(const zd *__restrict__ G, int ldg, int r, cons
 
 void launch_obs_final(const double *red, int r, const double *lam, double *out, cudaStream_t st) {
   ::lrei::count_launch();
-  obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), st>>>(red, r, lam, out);
+  obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), st>>>(red, r, lam, out, 0.0, 0.0, nullptr);
 }
 
 }  // namespace lrei
@@ -643,19 +701,26 @@ struct lrei_ctx {
   long long N = 0;
   int r_max = 0, r = 0;
   int model = 0, prec = 0;
-  double kappa = 0.0;
+  double kappa = 0.0;      // damping of the stored low-rank state: (1 - werner_p) kappa0
+  double kappa0 = 0.0;     // damping of the equation (lrei_create)
+  double werner_p = 0.0;   // weight of the identity part of rho (lrei_set_werner)
   bool fp64 = true;
   size_t elem = 16;
   cudaStream_t user = nullptr, st = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // second stream of the RK step: the stage algebra of stage j runs on it while the N-length
+  // passes of the later Krylov blocks run on st (events: fork, Krylov block j done, join)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_kry[4] = {};
+  int nsm_pass = 0;   // SMs the N-length passes of the RK step use (the rest serve the stage algebra)
+  int eig_sweeps = 30;   // FP64 Jacobi sweep limit of each partial eigendecomposition
   ModelArgs M;
   int KM = 0;   // leading dimension / capacity of the small k x k arrays
   // N x r blocks
   void *V = nullptr;
   void *blk[MAXB] = {};
   int nblk = 0;
-  void *Sbuf = nullptr;   // S = H Q_l of the current Krylov block (split mode)
-  bool fused_hv = false;
+  void *Sbuf = nullptr;   // S = H Q_l of the current Krylov block
   // device workspace
   double *partial = nullptr;
   double *red = nullptr;
@@ -689,9 +754,14 @@ struct lrei_ctx {
   std::vector<std::pair<void *, void *>> ab_hist;
   void *abQ[8] = {};       // Q_1 .. Q_{2m-1} of the AB basis (Q_0 = V)
   zd *Rraw = nullptr, *Bbar = nullptr, *tys[4] = {};
+  int *dead_frame = nullptr;   // frame columns decoupled as numerically dependent (AB basis)
+  // two-spin reduced density matrices: pair bit positions and per-pair results (device)
+  int *rdm_pairs = nullptr;
+  double *rdm_out = nullptr;
+  size_t partial_doubles = 0;   // capacity of `partial`
   bool ab_alloc = false;
   // adaptive step controller
-  int ctrl_judge_every = 8, ctrl_record = 0;
+  int ctrl_judge_every = 8, ctrl_judge_learned = 32, ctrl_record = 0;
   double ctrl_h = 0.0, ctrl_safety = 1.0, ctrl_calib = -1.0;
   long long st_accepted = 0, st_rejected = 0, st_judged = 0, st_rk4 = 0;
   double st_err_judged = 0.0;
@@ -702,6 +772,7 @@ struct lrei_ctx {
   lrei_mlp *net = nullptr;
   float *net_x = nullptr, *net_y = nullptr, *net_host = nullptr;
   int learned_fallback = 0;
+  double learn_corr = -1.0;   // judged error / network estimate at the last judge (learned rule)
 };
 
 namespace {
@@ -749,12 +820,12 @@ double tol_rc(const lrei_ctx *c) { return c->fp64 ? 1e-26 : 1e-13; }
 const double TOL_GAM = 1e-6;
 
 // One tall-skinny pass + deterministic reduction of its Gram into c->red.
-int ts_pass(lrei_ctx *c, TSArgs a) {
+int ts_pass(lrei_ctx *c, TSArgs a, int nsm = 0) {
   a.N = c->N;
   a.r = c->r;
   a.partial = c->partial;
   a.coef_scratch = c->coef_scratch;
-  int g = launch_ts(c->fp64, c->M, a, c->nsm, c->st);
+  int g = launch_ts(c->fp64, c->M, a, nsm > 0 ? nsm : c->nsm, c->st);
   if (g < 0) return LREI_ERR_ARG;
   launch_reduce(c->partial, g, (int)ts_partial_doubles(a.gram_left, c->r), c->red, c->st);
   return LREI_OK;
@@ -771,30 +842,77 @@ void set_gamma00(lrei_ctx *c) {
   sm_copy(c->L22, r, r, r, c->L, KM, c->st);
 }
 
+// Stage j of an RK step, on stream st2: the stage quantities in the orthonormal frame (G_j, X11,
+// W_j, Z_j), the stage matrix of K_{j+2} (or of rho_{k+1} for the last stage) and its top-r
+// eigenpairs.  It needs the frame of Q_0..Q_{j+1} only: with a = (j+2) r and b = (j+1) r,
+// Tbar[0:a, 0:b] = L_a^H Chat[0:a, 0:b] L_b^{-H}, because L is lower triangular and H Q_m lies
+// in span(Q_0..Q_{m+1}).
+void enqueue_stage(lrei_ctx *c, const Tableau &tb, int j, cudaStream_t st2) {
+  const int s = tb.s, r = c->r, KM = c->KM, K = (s + 1) * r;
+  const int a = (j + 2) * r, b = (j + 1) * r;
+  sm_conj_transpose(c->Chat, KM, a, b, c->Xh, KM, st2);
+  sm_trsv('N', c->L, KM, b, c->Xh, KM, a, st2);
+  sm_gemm('C', 'C', a, b, a, ONE, c->L, KM, c->Xh, KM, ZERO, c->Tbar, KM, st2);
+  sm_hermitize(c->Tbar, KM, b, st2);
+  // H V_j in the frame (ys[j] has no rows beyond b); rows a..K of ts are zero
+  if (a < K) sm_zero(c->ts + a, KM, K - a, r, st2);
+  sm_gemm('N', 'N', a, r, b, ONE, c->Tbar, KM, c->ys[j], KM, ZERO, c->ts, KM, st2);
+  sm_gemm('C', 'N', r, r, b, ONE, c->ys[j], KM, c->ts, KM, ZERO, c->G, r, st2);
+  ::lrei::count_launch();
+  stage_xwz_kernel<<<r, 128, 2 * r * sizeof(zd), st2>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->ys[j], c->ts, K,
+                                                        KM, c->X11, c->zs[j], c->wsv[j], j == 0 ? c->Gh : nullptr);
+  if (j == 0) {
+    ::lrei::count_launch();
+    feat_comm_kernel<<<1, 256, 0, st2>>>(c->ts, K, KM, c->Gh, r, c->lam0_dev, c->feat_dev);
+  }
+  StageCoefs C{};
+  C.nterms = j + 1;
+  const bool last = (j + 1 == s);
+  for (int l = 0; l <= j; ++l) C.c[l] = last ? tb.b[l] : tb.a[j + 1][l];
+  StagePtrs P{};
+  for (int l = 0; l <= j; ++l) {
+    P.y[l] = c->ys[l];
+    P.z[l] = c->zs[l];
+    P.w[l] = c->wsv[l];
+  }
+  const int nf = r * (1 + 2 * (j + 1));
+  const int kk = last ? K : (j + 2) * r;
+  ::lrei::count_launch();
+  stage_factors_kernel<<<64, 256, 0, st2>>>(P, C, c->lam0_dev, c->dt_dev, r, K, KM, c->Uf, c->Vf);
+  sm_gemm('N', 'C', kk, kk, nf, ONE, c->Uf, KM, c->Vf, KM, ZERO, c->Mm, KM, st2);
+  sm_hermitize(c->Mm, KM, kk, st2);
+  zd *dst = last ? c->yfin : c->ys[j + 1];
+  sm_zero(dst, KM, K, r, st2);
+  sm_eig_topr(c->Mm, KM, kk, r, dst, KM, c->mu_dev, c->eig_ws, c->status_dev, st2, c->eig_sweeps);
+}
+
 // Enqueue one RK step (scheme 0..3) on c->st.  Precondition: Gam/L leading r x r hold V^*V.
+// Krylov block l+1 (H.V, the Gram pass, the coefficients, the extension pass, the Cholesky
+// extension) runs on st; once it is done, stage l runs on st2 alongside Krylov block l+2.  The
+// N-length passes of the Krylov chain leave some SMs to the stage algebra (nsm_pass).  After the
+// last stage the streams join and st forms the new factor.
 int enqueue_rk_step(lrei_ctx *c, int scheme) {
   const Tableau &tb = kRK[scheme];
-  const int s = tb.s, r = c->r, KM = c->KM, K = (s + 1) * r, sr = s * r;
-  cudaStream_t st = c->st;
+  const int s = tb.s, r = c->r, KM = c->KM, K = (s + 1) * r;
+  cudaStream_t st = c->st, st2 = c->st2;
   zd *red = reinterpret_cast<zd *>(c->red);
+  LREI_CUDA_TRY(cudaEventRecord(c->ev_fork, st));
+  LREI_CUDA_TRY(cudaStreamWaitEvent(st2, c->ev_fork, 0));
+  sm_zero(c->ys[0], KM, K, r, st2);
+  sm_set_identity(c->ys[0], KM, r, r, st2);
   for (int l = 0; l < s; ++l) {
     const int k = (l + 1) * r, ldr = (l + 2) * r;
-    // pass A: S = H Q_l, P = [Q_0..Q_l]^* S, S^*S.  Split mode: S is formed once by the
-    // slab-major H.V kernel and both passes read it; fused mode recomputes H Q_l in each pass.
+    // pass A: S = H Q_l (formed once by the H.V kernel; both passes read it), then
+    // P = [Q_0..Q_l]^* S and S^*S
     TSArgs a{};
     a.nq = l + 1;
     a.gram_left = l + 1;
     for (int m = 0; m <= l; ++m) a.q[m] = qblock(c, m);
-    if (c->fused_hv) {
-      a.src = qblock(c, l);
-      a.apply_h = 1;
-    } else {
-      launch_hv(c->fp64, c->M, qblock(c, l), c->Sbuf, c->N, r, c->nsm, st, c->status_dev);
-      a.src = c->Sbuf;
-      a.apply_h = 0;
-    }
+    launch_hv(c->fp64, c->M, qblock(c, l), c->Sbuf, c->N, r, c->nsm_pass, st, c->status_dev);
+    a.src = c->Sbuf;
+    a.apply_h = 0;
     a.mode = 0;
-    int rc = ts_pass(c, a);
+    int rc = ts_pass(c, a, c->nsm_pass);
     if (rc) return rc;
     // C = Gamma^{-1} P
     sm_copy(red, ldr, k, r, c->Cc, KM, st);
@@ -817,7 +935,7 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
     b.coefS = c->Ainv;
     b.coefQ = c->coefQ;
     b.out = qblock(c, l + 1);
-    rc = ts_pass(c, b);
+    rc = ts_pass(c, b, c->nsm_pass);
     if (rc) return rc;
     sm_store_gram_cols(red, ldr, k, r, c->Gam, KM, st);
     // extend the Cholesky factor of Gamma
@@ -827,44 +945,15 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
     sm_gemm('C', 'N', r, r, k, MONE, c->Bs, KM, c->Bs, KM, ONE, c->Dm, r, st);
     sm_hermitize(c->Dm, r, r, st);
     sm_chol(c->Dm, r, r, c->L22, r, TOL_GAM, 1, c->dead_dev, c->status_dev, 0, st);
-    ::lrei::count_launch(); store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM);
+    ::lrei::count_launch(); store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM, 0,
+                                                                       nullptr);
+    // the frame of Q_0..Q_{l+1} is complete: stage l can run
+    LREI_CUDA_TRY(cudaEventRecord(c->ev_kry[l], st));
+    LREI_CUDA_TRY(cudaStreamWaitEvent(st2, c->ev_kry[l], 0));
+    enqueue_stage(c, tb, l, st2);
   }
-  // Tbar = L^H Chat L_s^{-H}: H Qbar_{0..s-1} = Qbar Tbar in the orthonormal frame Qbar = Q L^{-H}
-  sm_conj_transpose(c->Chat, KM, K, sr, c->Xh, KM, st);
-  sm_trsv('N', c->L, KM, sr, c->Xh, KM, K, st);
-  sm_gemm('C', 'C', K, sr, K, ONE, c->L, KM, c->Xh, KM, ZERO, c->Tbar, KM, st);
-  sm_hermitize(c->Tbar, KM, sr, st);
-  // stages
-  sm_zero(c->ys[0], KM, K, r, st);
-  sm_set_identity(c->ys[0], KM, r, r, st);
-  StagePtrs P{};
-  for (int j = 0; j < s; ++j) {
-    sm_gemm('N', 'N', K, r, sr, ONE, c->Tbar, KM, c->ys[j], KM, ZERO, c->ts, KM, st);
-    sm_gemm('C', 'N', r, r, sr, ONE, c->ys[j], KM, c->ts, KM, ZERO, c->G, r, st);
-    ::lrei::count_launch(); stage_xwz_kernel<<<r, 128, 2 * r * sizeof(zd), st>>>(c->G, r, c->lam0_dev, c->kappa, c->model, c->ys[j], c->ts, K,
-                                                         KM, c->X11, c->zs[j], c->wsv[j], j == 0 ? c->Gh : nullptr);
-    if (j == 0) {
-      ::lrei::count_launch();
-      feat_comm_kernel<<<1, 256, 0, st>>>(c->ts, K, KM, c->Gh, r, c->lam0_dev, c->feat_dev);
-    }
-    StageCoefs C{};
-    C.nterms = j + 1;
-    const bool last = (j + 1 == s);
-    for (int l = 0; l <= j; ++l) C.c[l] = last ? tb.b[l] : tb.a[j + 1][l];
-    for (int l = 0; l <= j; ++l) {
-      P.y[l] = c->ys[l];
-      P.z[l] = c->zs[l];
-      P.w[l] = c->wsv[l];
-    }
-    const int nf = r * (1 + 2 * (j + 1));
-    const int kk = last ? K : (j + 2) * r;
-    ::lrei::count_launch(); stage_factors_kernel<<<64, 256, 0, st>>>(P, C, c->lam0_dev, c->dt_dev, r, K, KM, c->Uf, c->Vf);
-    sm_gemm('N', 'C', kk, kk, nf, ONE, c->Uf, KM, c->Vf, KM, ZERO, c->Mm, KM, st);
-    sm_hermitize(c->Mm, KM, kk, st);
-    zd *dst = last ? c->yfin : c->ys[j + 1];
-    sm_zero(dst, KM, K, r, st);
-    sm_eig_topr(c->Mm, KM, kk, r, dst, KM, c->mu_dev, c->eig_ws, c->status_dev, st);
-  }
+  LREI_CUDA_TRY(cudaEventRecord(c->ev_join, st2));
+  LREI_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_join, 0));
   // V_{k+1} = Qbar Yfin = Q (L^{-H} Yfin), formed in place over Q_0 = V
   sm_copy(c->yfin, KM, K, r, c->Yc, KM, st);
   sm_trsv('C', c->L, KM, K, c->Yc, KM, r, st);
@@ -880,7 +969,7 @@ int enqueue_rk_step(lrei_ctx *c, int scheme) {
   if (rc) return rc;
   set_gamma00(c);
   ::lrei::count_launch(); check_small_kernel<<<1, 256, 0, st>>>(c->mu_dev, r, c->Gam, KM, c->status_dev);
-  ::lrei::count_launch(); feat_final_kernel<<<1, 32, 0, st>>>(c->mu_dev, c->lam0_dev, r, c->Gh, c->G, c->feat_dev);
+  ::lrei::count_launch(); feat_final_kernel<<<1, 256, 0, st>>>(c->mu_dev, c->lam0_dev, r, c->Gh, c->G, c->feat_dev);
   return LREI_OK;
 }
 
@@ -956,6 +1045,7 @@ int ab_prepare(lrei_ctx *c) {
   const size_t zs = sizeof(zd);
   if ((rc = dalloc_t(c, &c->Rraw, (size_t)c->KM * c->KM * zs))) return rc;
   if ((rc = dalloc_t(c, &c->Bbar, (size_t)c->KM * c->KM * zs))) return rc;
+  if ((rc = dalloc_t(c, &c->dead_frame, (size_t)c->KM * sizeof(int)))) return rc;
   for (int i = 0; i < 4; ++i)
     if ((rc = dalloc_t(c, &c->tys[i], (size_t)c->KM * c->r_max * zs))) return rc;
   c->ab_alloc = true;
@@ -995,8 +1085,15 @@ int ab_push_current(lrei_ctx *c) {
 }
 
 // One block of explicit Gram-Schmidt: raw block i against Q_0..Q_{i-1} (measured Gram), giving
-// Q_i, its Gram column, the extended Cholesky factor of Gamma, and raw = Q [C; Rc] in R.
-int orth_block(lrei_ctx *c, int i, const void *src, int apply_h, void *write_src, void *const *qb, zd *R) {
+// Q_i = raw_i - Q C (the residual, not normalised: its measured Gram column normalises it in the
+// frame), the extended Cholesky factor of Gamma, and the coordinates raw_i = Q [C; I] in R.
+// The history blocks are nearly dependent (consecutive states differ by O(h)), so their residuals
+// are small; normalising them by a residual Gram formed as S^*S - P^*C would cancel to the
+// rounding level of the complex64 Grams, while the Gram of the written residual is measured
+// directly.  A residual column that is numerically dependent on the earlier frame (Schur pivot
+// below TOL_GAM times its own squared norm) is decoupled: it keeps its projections in L and is
+// flagged in dead_frame so that the stage coordinates drop its leftover part.
+int orth_block(lrei_ctx *c, int i, const void *src, void *const *qb, zd *R) {
   const int r = c->r, KM = c->KM, k = i * r, ldr = (i + 1) * r;
   cudaStream_t st = c->st;
   zd *red = reinterpret_cast<zd *>(c->red);
@@ -1005,39 +1102,34 @@ int orth_block(lrei_ctx *c, int i, const void *src, int apply_h, void *write_src
   a.gram_left = i;
   for (int m = 0; m < i; ++m) a.q[m] = qb[m];
   a.src = src;
-  a.apply_h = apply_h;
+  a.apply_h = 0;
   a.mode = 0;
-  a.out = write_src;
   int rc = ts_pass(c, a);
   if (rc) return rc;
+  // C = Gamma^{-1} P; Q_i = raw_i - Q C
   sm_copy(red, ldr, k, r, c->Cc, KM, st);
   sm_trsv('N', c->L, KM, k, c->Cc, KM, r, st);
   sm_trsv('C', c->L, KM, k, c->Cc, KM, r, st);
-  sm_copy(red + k, ldr, r, r, c->GR, r, st);
-  sm_gemm('C', 'N', r, r, k, MONE, red, ldr, c->Cc, KM, ONE, c->GR, r, st);
-  sm_hermitize(c->GR, r, r, st);
-  sm_chol(c->GR, r, r, c->Lr, r, tol_rc(c), 0, c->dead_dev, c->status_dev, 0, st, red + k, ldr);
   sm_set_identity(c->Ainv, r, r, r, st);
-  sm_trsv('C', c->Lr, r, r, c->Ainv, r, r, st);
   sm_gemm('N', 'N', k, r, r, MONE, c->Cc, KM, c->Ainv, r, ZERO, c->coefQ, k, st);
   sm_copy(c->Cc, KM, k, r, R + (size_t)i * r * KM, KM, st);
-  ::lrei::count_launch(); store_rc_kernel<<<1, 256, 0, st>>>(c->Lr, r, c->dead_dev, R + (size_t)i * r * KM + k, KM);
+  sm_set_identity(R + (size_t)i * r * KM + k, KM, r, r, st);
   TSArgs b = a;
   b.mode = 1;
-  b.src = write_src ? write_src : src;
-  b.apply_h = write_src ? 0 : apply_h;
   b.out = qb[i];
   b.coefS = c->Ainv;
   b.coefQ = c->coefQ;
   if ((rc = ts_pass(c, b))) return rc;
   sm_store_gram_cols(red, ldr, k, r, c->Gam, KM, st);
+  // extend the Cholesky factor of Gamma: pivots judged against each column's own squared norm
   sm_copy(c->Gam + (size_t)k * KM, KM, k, r, c->Bs, KM, st);
   sm_trsv('N', c->L, KM, k, c->Bs, KM, r, st);
   sm_copy(c->Gam + (size_t)k * KM + k, KM, r, r, c->Dm, r, st);
   sm_gemm('C', 'N', r, r, k, MONE, c->Bs, KM, c->Bs, KM, ONE, c->Dm, r, st);
   sm_hermitize(c->Dm, r, r, st);
-  sm_chol(c->Dm, r, r, c->L22, r, TOL_GAM, 1, c->dead_dev, c->status_dev, 0, st);
-  ::lrei::count_launch(); store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM);
+  sm_chol(c->Dm, r, r, c->L22, r, TOL_GAM, 0, c->dead_dev, c->status_dev, 0, st, c->Gam + (size_t)k * KM + k, KM);
+  ::lrei::count_launch();
+  store_lrows_kernel<<<8, 256, 0, st>>>(c->Bs, KM, c->L22, r, k, c->dead_dev, c->L, KM, 1, c->dead_frame);
   return LREI_OK;
 }
 
@@ -1060,18 +1152,17 @@ int enqueue_ab_step(lrei_ctx *c, int m) {
   for (int i = 1; i < nb; ++i) qb[i] = c->abQ[i - 1];
   sm_zero(c->Rraw, KM, K, K, st);
   sm_set_identity(c->Rraw, KM, r, r, st);
+  LREI_CUDA_TRY(cudaMemsetAsync(c->dead_frame, 0, (size_t)K * sizeof(int), st));
   for (int i = 1; i < nb; ++i) {
-    int rc;
-    if (i == 1 && !c->fused_hv) {
-      launch_hv(c->fp64, c->M, c->V, yk, c->N, r, c->nsm, st, c->status_dev);
-      rc = orth_block(c, 1, yk, 0, nullptr, qb, c->Rraw);
-    } else {
-      rc = (i == 1) ? orth_block(c, 1, c->V, 1, yk, qb, c->Rraw) : orth_block(c, i, raw[i], 0, nullptr, qb, c->Rraw);
-    }
+    if (i == 1) launch_hv(c->fp64, c->M, c->V, yk, c->N, r, c->nsm, st, c->status_dev);
+    const int rc = orth_block(c, i, raw[i], qb, c->Rraw);
     if (rc) return rc;
   }
-  // coordinates of the raw blocks in the orthonormal frame Qbar = Q L^{-H}: Bbar = L^H Rraw
+  // coordinates of the raw blocks in the orthonormal frame Qbar = Q L^{-H}: Bbar = L^H Rraw, without
+  // the leftover parts of dead columns
   sm_gemm('C', 'N', K, K, K, ONE, c->L, KM, c->Rraw, KM, ZERO, c->Bbar, KM, st);
+  ::lrei::count_launch();
+  zero_dead_rows_kernel<<<8, 256, 0, st>>>(c->Bbar, KM, K, K, c->dead_frame);
   for (int l = 0; l < m; ++l) {
     // the state of step k-l is V_l orthonormalised: vbar = v Lv^{-H}, H vbar = y Lv^{-H}
     sm_copy(c->Bbar + (size_t)(2 * l) * r * KM, KM, K, r, c->ys[l], KM, st);
@@ -1099,7 +1190,7 @@ int enqueue_ab_step(lrei_ctx *c, int m) {
   sm_gemm('N', 'C', K, K, r * (1 + 2 * m), ONE, c->Uf, KM, c->Vf, KM, ZERO, c->Mm, KM, st);
   sm_hermitize(c->Mm, KM, K, st);
   sm_zero(c->yfin, KM, K, r, st);
-  sm_eig_topr(c->Mm, KM, K, r, c->yfin, KM, c->mu_dev, c->eig_ws, c->status_dev, st);
+  sm_eig_topr(c->Mm, KM, K, r, c->yfin, KM, c->mu_dev, c->eig_ws, c->status_dev, st, c->eig_sweeps);
   sm_copy(c->yfin, KM, K, r, c->Yc, KM, st);
   sm_trsv('C', c->L, KM, K, c->Yc, KM, r, st);
   sm_copy(c->Yc, KM, K, r, c->coefQ, K, st);
@@ -1127,8 +1218,17 @@ int enqueue_ab_step(lrei_ctx *c, int m) {
 // step, and after any rejection, the estimate is replaced by step doubling (one step of h
 // against two of h/2, error = 16/15 ||rho_h - rho_{h/2,h/2}||_F / ||rho||_F), which also
 // recalibrates the drift factor.  h_new = h clip(0.9 (tol/err)^(1/5), 0.2, 5); a step whose
-// error exceeds tol is rejected and retried.  The learned rule predicts log(h_new/h) from
-// step features with the controller network and keeps the plain judge as fallback.
+// error exceeds tol is rejected and retried.  The learned rule replaces the calibrated drift by
+// the controller network's estimate of the step's local error (from the step's features: the
+// spectrum, the drift, h, ||[rho,H]||^2, the stage spread, kappa, the model, tol, r), so it needs
+// the step-doubling judge four times less often (every 4 judge_every steps, after a rejection,
+// and when no estimate is available).  Its estimate is scaled by a correction factor refitted at
+// every judge (judged error / network estimate), so a shift of the whole error scale (another
+// system size, another tolerance) is absorbed at the first judge and the network only has to
+// follow the variation between judges.  The same formula turns either estimate into the next h.
+// A judge that finds the error more than 3x above the corrected estimate hands control to the
+// plain rule for the next 16 steps; an estimate above tol, or more than 10x below the calibrated
+// drift, is judged before it is used.
 constexpr int NFEAT = 40;
 
 int ctrl_prepare(lrei_ctx *c) {
@@ -1227,6 +1327,23 @@ int judge(lrei_ctx *c, double h, double *err) {
   return LREI_OK;
 }
 
+// Local error estimate of the learned rule for the step just taken: the network maps the step's
+// features to log(err / drift), the ratio of the local error to the spectral drift of the
+// unprojected rho_{k+1}.  Returns a negative value when no estimate is available.
+int learned_estimate(lrei_ctx *c, const double *f, double hs, double tol, double *err) {
+  float x[NFEAT];
+  build_features(c, f, hs, tol, x);
+  std::memcpy(c->net_host, x, sizeof(x));
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->net_x, c->net_host, sizeof(x), cudaMemcpyHostToDevice, c->st));
+  int rc = lrei_mlp_forward_on(c->net, c->net_x, 1, c->net_y, c->st);   // on the context's stream
+  if (rc) return rc;
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->net_host, c->net_y, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  const double e = std::exp((double)c->net_host[0]) * f[2];
+  *err = (std::isfinite(e) && f[2] > 0) ? e : -1.0;
+  return LREI_OK;
+}
+
 int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
   int rc = build_graph(c, (int)LREI_RK4);
   if (rc) return rc;
@@ -1235,10 +1352,8 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
   tol = std::fmax(tol, c->fp64 ? LREI_TOL_FLOOR_FP64 : LREI_TOL_FLOOR_MIXED);
   const double h_min = 1e-12 * std::fmax(1.0, std::fabs(t_end));
   int rejected_in_row = 0;
-  int since_judge = c->ctrl_judge_every;   // the first step is judged
+  int since_judge = 1 << 30;   // the first step is judged
   bool last_rejected = false;
-  bool net_chose_h = false;   // the step being taken has the size the network proposed
-  int accepted_flag = 1;
   double f[3];
   while (c->t < t_end - 1e-12 * std::fmax(1.0, std::fabs(t_end))) {
     const double hs = std::fmin(h, t_end - c->t);
@@ -1250,8 +1365,18 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
     if (sbits & (ST_NONFINITE | ST_RANK)) return status_to_code(sbits);
     const double drift = f[2];
     ++since_judge;
-    const bool do_judge = since_judge >= c->ctrl_judge_every || last_rejected || c->ctrl_calib < 0 ||
-                          (controller == 1 && c->learned_fallback > 0 && since_judge >= 2);
+    // the learned rule is in charge unless a judged step caught it underestimating the error
+    const bool learned = controller == 1 && c->net && c->learned_fallback <= 0;
+    double err_net = -1.0;
+    if (learned && (rc = learned_estimate(c, f, hs, tol, &err_net))) return rc;
+    const int period = learned ? c->ctrl_judge_learned : c->ctrl_judge_every;
+    const double err_plain = (c->ctrl_calib > 0 ? c->ctrl_calib : 1.0) * drift;
+    // the network's estimate times its correction factor (refitted at every judge)
+    const double err_learn = err_net >= 0 ? (c->learn_corr > 0 ? c->learn_corr : 1.0) * err_net : -1.0;
+    // an estimate far below the calibrated drift, or above tol, is checked by a judge before it
+    // is used (a step is never rejected on the network's word alone)
+    const bool doubtful = learned && (err_learn < 0 || err_learn < 0.1 * err_plain || err_learn > tol);
+    const bool do_judge = since_judge >= period || last_rejected || c->ctrl_calib < 0 || doubtful;
     double err;
     c->st_rk4 += 1;
     if (do_judge) {
@@ -1261,8 +1386,13 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       c->st_err_judged = err;
       since_judge = 0;
       if (drift > 0) c->ctrl_calib = err / drift;
+      if (learned && err_net > 0) {
+        // an estimate more than 3x below the judged error sends control to the plain rule
+        if (err_learn > 0 && c->learn_corr > 0 && err > 3.0 * err_learn) c->learned_fallback = 16;
+        c->learn_corr = err / err_net;
+      }
     } else {
-      err = (c->ctrl_calib > 0 ? c->ctrl_calib : 1.0) * drift;
+      err = learned ? err_learn : err_plain;
     }
     if (c->ctrl_record) {
       float x[NFEAT];
@@ -1273,16 +1403,13 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
       c->records.push_back(do_judge ? err : -1.0);
       c->records.push_back(err <= tol ? 1.0 : 0.0);
     }
+    if (c->learned_fallback > 0) --c->learned_fallback;
+    const double ratio = std::fmin(5.0, std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2)));
     if (!(err <= tol)) {
       restore_state(c, c->Vsave, c->Gsave, c->Lsave);
       c->st_rejected += 1;
-      h = hs * std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2));
+      h = hs * std::fmin(ratio, 0.9);
       last_rejected = true;
-      accepted_flag = 0;
-      // a rejected step whose size came from the network (by the judge or by the drift
-      // estimate) hands control to the plain rule for the next 16 steps
-      if (controller == 1 && (do_judge || net_chose_h)) c->learned_fallback = 16;
-      net_chose_h = false;
       if (++rejected_in_row >= 64 || h < h_min) {
         c->ctrl_h = h;
         return LREI_ERR_STEP;
@@ -1293,27 +1420,6 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
     c->st_accepted += 1;
     rejected_in_row = 0;
     last_rejected = false;
-    accepted_flag = 1;
-    double ratio = std::fmin(5.0, std::fmax(0.2, 0.9 * std::pow(tol / std::fmax(err, 1e-300), 0.2)));
-    net_chose_h = false;
-    if (controller == 1 && c->net && c->learned_fallback <= 0) {
-      float x[NFEAT];
-      build_features(c, f, hs, tol, x);
-      std::memcpy(c->net_host, x, sizeof(x));
-      LREI_CUDA_TRY(cudaMemcpyAsync(c->net_x, c->net_host, sizeof(x), cudaMemcpyHostToDevice, c->st));
-      // the network runs on the context's stream
-      if ((rc = lrei_mlp_forward_on(c->net, c->net_x, 1, c->net_y, c->st))) return rc;
-      LREI_CUDA_TRY(cudaMemcpyAsync(c->net_host, c->net_y, sizeof(float), cudaMemcpyDeviceToHost, c->st));
-      LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
-      const double pred = std::exp((double)c->net_host[0]);
-      if (std::isfinite(pred)) {
-        // trust region around the plain rule's ratio: the network may shrink the step freely
-        // and grow it at most 25% beyond the plain choice (and never more than 2x per step)
-        ratio = std::fmin(std::fmin(2.0, 1.25 * ratio), std::fmax(0.2, pred));
-        net_chose_h = true;
-      }
-    }
-    if (c->learned_fallback > 0) --c->learned_fallback;
     h = hs * ratio;
     if (h < h_min) {
       c->ctrl_h = h;
@@ -1326,13 +1432,49 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
 
 }  // namespace
 
+namespace lrei {
+int build_model_args(int n, const void *bonds, const double B[3], ModelArgs *M) {
+  const lrei_bonds *J = static_cast<const lrei_bonds *>(bonds);
+  if (n < 1 || n > MAX_SPINS) return LREI_ERR_ARG;
+  double Bv[3] = {0, 0, 0};
+  if (B) for (int i = 0; i < 3; ++i) Bv[i] = B[i];
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(Bv[i])) return LREI_ERR_NONFINITE;
+  const int nb = J ? J->nbonds : 0;
+  if (nb < 0 || nb > MAX_BONDS) return LREI_ERR_ARG;
+  if (nb > 0 && (!J->site_i || !J->site_j || !J->jxy || !J->jz)) return LREI_ERR_ARG;
+  std::memset(M, 0, sizeof(*M));
+  M->n = n;
+  M->nb = nb;
+  M->bx = Bv[0];
+  M->by = Bv[1];
+  M->bz = Bv[2];
+  M->cplx = (Bv[0] != 0.0 || Bv[1] != 0.0) ? 1 : 0;
+  double c0 = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    const int i = J->site_i[b], j = J->site_j[b];
+    if (i < 0 || i >= n || j < 0 || j >= n || i == j) return LREI_ERR_ARG;
+    if (!std::isfinite(J->jxy[b]) || !std::isfinite(J->jz[b])) return LREI_ERR_NONFINITE;
+    // site i is bit n-1-i of the basis index (site 0 = most significant bit)
+    M->bi[b] = (uint8_t)(n - 1 - i);
+    M->bj[b] = (uint8_t)(n - 1 - j);
+    M->mask[b] = (1u << (n - 1 - i)) | (1u << (n - 1 - j));
+    M->jxy[b] = J->jxy[b];
+    M->jz[b] = J->jz[b];
+    c0 += 0.5 * J->jz[b];
+  }
+  M->c0 = c0;
+  return LREI_OK;
+}
+}  // namespace lrei
+
 extern "C" {
 
 const char *lrei_error_string(int code) {
   switch (code) {
     case LREI_OK: return "ok";
     case LREI_ERR_ARG: return "invalid argument";
-    case LREI_ERR_UNSUPPORTED: return "unsupported physics in this build (transverse field)";
+    case LREI_ERR_UNSUPPORTED: return "unsupported in this build";
     case LREI_ERR_NONFINITE: return "non-finite value in input or state";
     case LREI_ERR_TRACE: return "spectrum must be >= 0 and sum to 1";
     case LREI_ERR_RANK: return "rank-deficient factor";
@@ -1355,42 +1497,19 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   if (model != LREI_QLL && model != LREI_QLLG) return LREI_ERR_ARG;
   if (prec != LREI_FP64 && prec != LREI_MIXED_C64) return LREI_ERR_ARG;
   if ((long long)r_max > (1LL << n)) return LREI_ERR_ARG;
-  double Bv[3] = {0, 0, 0};
-  if (B) for (int i = 0; i < 3; ++i) Bv[i] = B[i];
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(Bv[i])) return LREI_ERR_NONFINITE;
-  if (Bv[0] != 0.0 || Bv[1] != 0.0) return LREI_ERR_UNSUPPORTED;
-  const int nb = J ? J->nbonds : 0;
-  if (nb < 0 || nb > MAX_BONDS) return LREI_ERR_ARG;
-  if (nb > 0 && (!J->site_i || !J->site_j || !J->jxy || !J->jz)) return LREI_ERR_ARG;
+  ModelArgs Mk;
+  const int mrc = build_model_args(n, J, B, &Mk);
+  if (mrc != LREI_OK) return mrc;
   lrei_ctx *c = new (std::nothrow) lrei_ctx();
   if (!c) return LREI_ERR_OOM;
-  std::memset(&c->M, 0, sizeof(c->M));
-  c->M.n = n;
-  c->M.nb = nb;
-  c->M.bz = Bv[2];
-  double c0 = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    const int i = J->site_i[b], j = J->site_j[b];
-    if (i < 0 || i >= n || j < 0 || j >= n || i == j || !std::isfinite(J->jxy[b]) || !std::isfinite(J->jz[b])) {
-      delete c;
-      return LREI_ERR_ARG;
-    }
-    // site i is bit n-1-i of the basis index (site 0 = most significant bit)
-    c->M.bi[b] = (uint8_t)(n - 1 - i);
-    c->M.bj[b] = (uint8_t)(n - 1 - j);
-    c->M.mask[b] = (1u << (n - 1 - i)) | (1u << (n - 1 - j));
-    c->M.jxy[b] = J->jxy[b];
-    c->M.jz[b] = J->jz[b];
-    c0 += 0.5 * J->jz[b];
-  }
-  c->M.c0 = c0;
+  c->M = Mk;
   c->n = n;
   c->N = 1LL << n;
   c->r_max = r_max;
   c->model = model;
   c->prec = prec;
   c->kappa = lambda;
+  c->kappa0 = lambda;
   c->fp64 = (prec == LREI_FP64);
   c->elem = c->fp64 ? 16 : 8;
   c->user = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -1402,8 +1521,14 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   if (cudaGetDevice(&c->dev) != cudaSuccess) return fail(LREI_ERR_CUDA);
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
   if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) return fail(LREI_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) return fail(LREI_ERR_CUDA);
   cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+  for (int i = 0; i < 4; ++i) cudaEventCreateWithFlags(&c->ev_kry[i], cudaEventDisableTiming);
+  // the N-length passes of the RK step leave one SM in sixteen to the stage algebra running beside them
+  c->nsm_pass = c->nsm - std::max(1, c->nsm / 16);
   if (ts_init() || sm_init()) return fail(LREI_ERR_CUDA);
   {
     const int lim = 100 * 1024;
@@ -1419,11 +1544,13 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   for (int i = 0; i < c->nblk; ++i)
     if ((rc = dalloc(c, &c->blk[i], blk_bytes))) return fail(rc);
   if ((rc = dalloc(c, &c->Sbuf, blk_bytes))) return fail(rc);
-  c->fused_hv = getenv("LREI_FUSED_HV") != nullptr;
   c->KM = 8 * r_max;   // RK_s needs (s+1) r <= 5 r, AB_m needs 2 m r <= 8 r
   const int KM = c->KM, R = r_max;
   const size_t zs = sizeof(zd);
-  if ((rc = dalloc_t(c, &c->partial, (size_t)(ts_max_grid(c->nsm) + 16) * (MAXB + 1) * R * R * 2 * sizeof(double)))) return fail(rc);
+  c->partial_doubles = (size_t)(ts_max_grid(c->nsm) + 16) * (MAXB + 1) * R * R * 2;
+  if ((rc = dalloc_t(c, &c->partial, c->partial_doubles * sizeof(double)))) return fail(rc);
+  if ((rc = dalloc_t(c, &c->rdm_pairs, 2 * LREI_RDM_MAX_PAIRS * sizeof(int)))) return fail(rc);
+  if ((rc = dalloc_t(c, &c->rdm_out, (size_t)34 * LREI_RDM_MAX_PAIRS * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->red, (size_t)(MAXB + 1) * R * R * 2 * sizeof(double)))) return fail(rc);
   if ((rc = dalloc(c, &c->coef_scratch, (size_t)(MAXB + 1) * MAX_R * MAX_R * zs))) return fail(rc);
   zd **kk[] = {&c->Gam, &c->L, &c->Chat, &c->Tbar, &c->Xh, &c->Mm};
@@ -1446,13 +1573,13 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   if ((rc = dalloc_t(c, &c->lam0_dev, R * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->mu_dev, R * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->dt_dev, sizeof(double)))) return fail(rc);
-  if ((rc = dalloc_t(c, &c->obs_dev, 16 * sizeof(double)))) return fail(rc);
+  if ((rc = dalloc_t(c, &c->obs_dev, 128 * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->feat_dev, 16 * sizeof(double)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->status_dev, sizeof(int)))) return fail(rc);
   if ((rc = dalloc_t(c, &c->dead_dev, R * sizeof(int)))) return fail(rc);
   if ((rc = dalloc(c, &c->eig_ws, sm_eig_ws_bytes(KM, R)))) return fail(rc);
   if (cudaMallocHost(&c->status_host, sizeof(int)) != cudaSuccess) return fail(LREI_ERR_OOM);
-  if (cudaMallocHost(&c->obs_host, 16 * sizeof(double)) != cudaSuccess) return fail(LREI_ERR_OOM);
+  if (cudaMallocHost(&c->obs_host, 128 * sizeof(double)) != cudaSuccess) return fail(LREI_ERR_OOM);
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(LREI_ERR_CUDA);
   *out = c;
   return LREI_OK;
@@ -1461,12 +1588,18 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
 int lrei_destroy(lrei_ctx *c) {
   if (!c) return LREI_OK;
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->st2) cudaStreamSynchronize(c->st2);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   for (void *p : c->allocs) cudaFree(p);
   if (c->status_host) cudaFreeHost(c->status_host);
   if (c->obs_host) cudaFreeHost(c->obs_host);
   if (c->ev_in) cudaEventDestroy(c->ev_in);
   if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (int i = 0; i < 4; ++i)
+    if (c->ev_kry[i]) cudaEventDestroy(c->ev_kry[i]);
+  if (c->st2) cudaStreamDestroy(c->st2);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
   return LREI_OK;
@@ -1613,9 +1746,11 @@ int lrei_step_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
 int lrei_controller_config(lrei_ctx *c, int judge_every, int record, double h0) {
   if (!c || judge_every < 1) return LREI_ERR_ARG;
   c->ctrl_judge_every = judge_every;
+  c->ctrl_judge_learned = judge_every < (1 << 26) ? 4 * judge_every : judge_every;
   c->ctrl_record = record ? 1 : 0;
   if (h0 > 0) c->ctrl_h = h0;
   c->ctrl_calib = -1.0;
+  c->learn_corr = -1.0;
   c->records.clear();
   c->st_accepted = c->st_rejected = c->st_judged = c->st_rk4 = 0;
   return LREI_OK;
@@ -1656,10 +1791,10 @@ int lrei_observables(lrei_ctx *c, lrei_obs *out) {
   enter(c);
   int g = launch_obs(c->fp64, c->M, c->V, c->N, r, c->partial, c->nsm, c->st);
   launch_reduce(c->partial, g, 6 * r * r * 2, c->red, c->st);
-  ::lrei::count_launch(); obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), c->st>>>(c->red, r, c->lam0_dev, c->obs_dev);
-  LREI_CUDA_TRY(cudaMemcpyAsync(c->obs_host, c->obs_dev, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-  std::vector<double> mu(r);
-  LREI_CUDA_TRY(cudaMemcpyAsync(mu.data(), c->mu_dev, r * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  ::lrei::count_launch();
+  obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), c->st>>>(c->red, r, c->lam0_dev, c->obs_dev, c->werner_p,
+                                                               1.0 / (double)c->N, c->mu_dev);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->obs_host, c->obs_dev, 80 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   leave(c);
   LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
   std::memset(out, 0, sizeof(*out));
@@ -1674,10 +1809,55 @@ int lrei_observables(lrei_ctx *c, lrei_obs *out) {
   out->herm_err = c->obs_host[7];
   out->comm_norm = c->obs_host[8];
   out->r = r;
-  for (int i = 0; i < r && i < 64; ++i) {
-    out->ritz[i] = mu[i];
-    out->lambda0[i] = c->lam0[i];
+  for (int i = 0; i < r && i < 32; ++i) {
+    out->ritz[i] = c->obs_host[16 + i];
+    out->lambda0[i] = c->obs_host[48 + i];
   }
+  return LREI_OK;
+}
+
+int lrei_set_eig_sweeps(lrei_ctx *c, int max_sweeps) {
+  if (!c || max_sweeps < 1 || max_sweeps > 100) return LREI_ERR_ARG;
+  c->eig_sweeps = max_sweeps;
+  if (c->gexec) {   // the limit is a kernel argument of the captured step
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_scheme = -1;
+  }
+  return LREI_OK;
+}
+
+int lrei_set_dmi(lrei_ctx *c, int nbonds, const double *dz) {
+  if (!c || nbonds != c->M.nb || (nbonds > 0 && !dz)) return LREI_ERR_ARG;
+  for (int k = 0; k < nbonds; ++k)
+    if (!std::isfinite(dz[k])) return LREI_ERR_NONFINITE;
+  bool any = c->M.bx != 0.0 || c->M.by != 0.0;
+  for (int k = 0; k < nbonds; ++k) {
+    c->M.dz[k] = dz[k];
+    any = any || dz[k] != 0.0;
+  }
+  c->M.cplx = any ? 1 : 0;
+  // the model is a kernel argument of the captured step and of the multistep history
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_scheme = -1;
+  }
+  if (c->ab_alloc) ab_clear(c);
+  return LREI_OK;
+}
+
+int lrei_set_werner(lrei_ctx *c, double p) {
+  if (!c || !std::isfinite(p) || p < 0.0 || p >= 1.0) return LREI_ERR_ARG;
+  c->werner_p = p;
+  c->kappa = (1.0 - p) * c->kappa0;
+  // the damping is a kernel argument of the captured step and of the multistep history
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_scheme = -1;
+  }
+  if (c->ab_alloc) ab_clear(c);
   return LREI_OK;
 }
 
@@ -1862,6 +2042,227 @@ int lrei_householder(lrei_ctx *c, void *U_dev, double *T_host, double *D_host) {
   leave(c);
   LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
   return status_to_code(read_status(c));
+}
+
+int lrei_two_spin_rdm(lrei_ctx *c, int npairs, const int *site_k, const int *site_l, double *R_host,
+                      double *concurrence_host, double *negativity_host) {
+  if (!c || npairs < 1 || npairs > LREI_RDM_MAX_PAIRS || !site_k || !site_l) return LREI_ERR_ARG;
+  if (!c->has_state) return LREI_ERR_STATE;
+  if (c->n < 2) return LREI_ERR_ARG;
+  std::vector<int> bits(2 * (size_t)npairs);
+  for (int q = 0; q < npairs; ++q) {
+    const int k = site_k[q], l = site_l[q];
+    if (k < 0 || k >= c->n || l < 0 || l >= c->n || k == l) return LREI_ERR_ARG;
+    bits[2 * q] = c->n - 1 - k;   // site i is bit n-1-i of the basis index
+    bits[2 * q + 1] = c->n - 1 - l;
+  }
+  const int r = c->r;
+  enter(c);
+  // the orthonormalised factor Vb = V L^{-H} (V^*V = L L^H) into the scratch block
+  sm_set_identity(c->Ainv, r, r, r, c->st);
+  sm_trsv('C', c->L, c->KM, r, c->Ainv, r, r, c->st);
+  TSArgs cmb{};
+  cmb.nq = 1;
+  cmb.gram_left = 0;
+  cmb.q[0] = c->V;
+  cmb.coefQ = c->Ainv;
+  cmb.mode = 2;
+  cmb.out = c->Sbuf;
+  int rc = ts_pass(c, cmb);
+  if (rc) { leave(c); return rc; }
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->rdm_pairs, bits.data(), bits.size() * sizeof(int), cudaMemcpyHostToDevice, c->st));
+  // CTAs per pair: enough to fill the GPU for a few pairs, bounded by the partial-sum buffer
+  const long long groups = c->N / 4;
+  const long long per_cta = 256 / r;
+  int ncta = (int)std::min<long long>(64, std::max<long long>(1, (groups + per_cta - 1) / per_cta));
+  int chunk = (int)std::min<size_t>((size_t)npairs, c->partial_doubles / ((size_t)ncta * 20));
+  while (chunk < 1 && ncta > 1) {
+    ncta /= 2;
+    chunk = (int)std::min<size_t>((size_t)npairs, c->partial_doubles / ((size_t)ncta * 20));
+  }
+  for (int q0 = 0; q0 < npairs && !rc; q0 += chunk) {
+    const int nq = std::min(chunk, npairs - q0);
+    if (launch_rdm(c->fp64, c->Sbuf, c->N, r, c->lam0_dev, c->rdm_pairs + 2 * q0, nq, c->partial, ncta, c->st))
+      rc = LREI_ERR_ARG;
+    else
+      launch_rdm_final(c->partial, ncta, nq, c->werner_p, c->rdm_out + (size_t)34 * q0, c->st);
+  }
+  std::vector<double> res((size_t)34 * npairs);
+  if (!rc)
+    LREI_CUDA_TRY(cudaMemcpyAsync(res.data(), c->rdm_out, res.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  leave(c);
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (rc) return rc;
+  for (int q = 0; q < npairs; ++q) {
+    if (R_host) std::memcpy(R_host + (size_t)32 * q, res.data() + (size_t)34 * q, 32 * sizeof(double));
+    if (concurrence_host) concurrence_host[q] = res[(size_t)34 * q + 32];
+    if (negativity_host) negativity_host[q] = res[(size_t)34 * q + 33];
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? LREI_OK : cuda_fail(e, "two_spin_rdm");
+}
+
+int lrei_truncate_rank(lrei_ctx *c, double tol_r, int *r_out, double *dropped_out) {
+  if (!c || !std::isfinite(tol_r) || tol_r < 0.0) return LREI_ERR_ARG;
+  if (!c->has_state) return LREI_ERR_STATE;
+  const int r = c->r;
+  // keep the leading k eigenvalues: the trailing ones (smallest, Lambda_0 is decreasing) go while
+  // their cumulative weight stays within tol_r; at least one is kept
+  int k = r;
+  double w = 0.0;
+  while (k > 1 && w + c->lam0[k - 1] <= tol_r) w += c->lam0[--k];
+  if (r_out) *r_out = k;
+  if (dropped_out) *dropped_out = w;
+  if (k == r) return LREI_OK;
+  enter(c);
+  const long long total = c->N * k;
+  const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  ::lrei::count_launch();
+  if (c->fp64) keep_cols_kernel<double><<<grid, 256, 0, c->st>>>((const cx<double> *)c->V, r, (cx<double> *)c->Sbuf, k, c->N);
+  else keep_cols_kernel<float><<<grid, 256, 0, c->st>>>((const cx<float> *)c->V, r, (cx<float> *)c->Sbuf, k, c->N);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->V, c->Sbuf, (size_t)total * c->elem, cudaMemcpyDeviceToDevice, c->st));
+  c->r = k;
+  // the kept weights are renormalised to trace one
+  for (int i = 0; i < k; ++i) c->lam0[i] /= (1.0 - w);
+  c->lam0.resize(k);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->lam0_dev, c->lam0.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->mu_dev, c->lam0.data(), k * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  // the Gram of the kept columns is the leading block of the old one; measured again all the same
+  TSArgs a{};
+  a.nq = 0;
+  a.gram_left = 0;
+  a.src = c->V;
+  a.apply_h = 0;
+  a.mode = 0;
+  int rc = ts_pass(c, a);
+  if (!rc) {
+    LREI_CUDA_TRY(cudaMemsetAsync(c->L, 0, (size_t)c->KM * c->KM * sizeof(zd), c->st));
+    set_gamma00(c);
+  }
+  if (c->ab_alloc) ab_clear(c);
+  const int s = read_status(c);
+  leave(c);
+  if (rc) return rc;
+  return status_to_code(s);
+}
+
+// ---- checkpoint: everything the next steps read, byte for byte
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int version, n, r, prec, model, ab_m, nhist, pad;
+  double t, ab_dt, kappa0, werner_p, ctrl_h, ctrl_calib;
+};
+size_t ckpt_bytes(const lrei_ctx *c) {
+  const size_t blk = (size_t)c->N * c->r * c->elem;
+  const size_t nh = c->ab_alloc ? c->ab_hist.size() : 0;
+  return sizeof(CkptHeader) + 2 * (size_t)c->r * sizeof(double) + 2 * (size_t)c->r * c->r * sizeof(zd) + blk +
+         2 * nh * blk;
+}
+}  // namespace
+
+long long lrei_checkpoint_bytes(lrei_ctx *c) {
+  if (!c || !c->has_state) return 0;
+  return (long long)ckpt_bytes(c);
+}
+
+int lrei_checkpoint_save(lrei_ctx *c, void *buf, long long bytes) {
+  if (!c || !buf) return LREI_ERR_ARG;
+  if (!c->has_state) return LREI_ERR_STATE;
+  if (bytes < (long long)ckpt_bytes(c)) return LREI_ERR_ARG;
+  const int r = c->r, KM = c->KM;
+  const size_t blk = (size_t)c->N * r * c->elem;
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "LREICKP", 8);
+  h.version = 1;
+  h.n = c->n;
+  h.r = r;
+  h.prec = c->prec;
+  h.model = c->model;
+  h.ab_m = c->ab_alloc ? c->ab_m : 0;
+  h.nhist = c->ab_alloc ? (int)c->ab_hist.size() : 0;
+  h.t = c->t;
+  h.ab_dt = c->ab_dt;
+  h.kappa0 = c->kappa0;
+  h.werner_p = c->werner_p;
+  h.ctrl_h = c->ctrl_h;
+  h.ctrl_calib = c->ctrl_calib;
+  unsigned char *p = static_cast<unsigned char *>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  std::memcpy(p, c->lam0.data(), r * sizeof(double));
+  p += r * sizeof(double);
+  enter(c);
+  LREI_CUDA_TRY(cudaMemcpyAsync(p, c->mu_dev, r * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  p += r * sizeof(double);
+  LREI_CUDA_TRY(cudaMemcpy2DAsync(p, r * sizeof(zd), c->Gam, KM * sizeof(zd), r * sizeof(zd), r, cudaMemcpyDeviceToHost, c->st));
+  p += (size_t)r * r * sizeof(zd);
+  LREI_CUDA_TRY(cudaMemcpy2DAsync(p, r * sizeof(zd), c->L, KM * sizeof(zd), r * sizeof(zd), r, cudaMemcpyDeviceToHost, c->st));
+  p += (size_t)r * r * sizeof(zd);
+  LREI_CUDA_TRY(cudaMemcpyAsync(p, c->V, blk, cudaMemcpyDeviceToHost, c->st));
+  p += blk;
+  for (int i = 0; i < h.nhist; ++i) {
+    LREI_CUDA_TRY(cudaMemcpyAsync(p, c->ab_hist[i].first, blk, cudaMemcpyDeviceToHost, c->st));
+    p += blk;
+    LREI_CUDA_TRY(cudaMemcpyAsync(p, c->ab_hist[i].second, blk, cudaMemcpyDeviceToHost, c->st));
+    p += blk;
+  }
+  leave(c);
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  return LREI_OK;
+}
+
+int lrei_checkpoint_load(lrei_ctx *c, const void *buf, long long bytes) {
+  if (!c || !buf || bytes < (long long)sizeof(CkptHeader)) return LREI_ERR_ARG;
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, "LREICKP", 8) != 0 || h.version != 1) return LREI_ERR_ARG;
+  if (h.n != c->n || h.prec != c->prec || h.model != c->model || h.r < 1 || h.r > c->r_max || h.nhist < 0 ||
+      h.nhist > 3 || h.kappa0 != c->kappa0)
+    return LREI_ERR_ARG;
+  const int r = h.r, KM = c->KM;
+  const size_t blk = (size_t)c->N * r * c->elem;
+  const size_t need = sizeof(h) + 2 * (size_t)r * sizeof(double) + 2 * (size_t)r * r * sizeof(zd) + blk +
+                      2 * (size_t)h.nhist * blk;
+  if ((size_t)bytes < need) return LREI_ERR_ARG;
+  int rc;
+  if (h.nhist > 0 && (rc = ab_prepare(c))) return rc;
+  const unsigned char *p = static_cast<const unsigned char *>(buf) + sizeof(h);
+  c->r = r;
+  c->lam0.assign(reinterpret_cast<const double *>(p), reinterpret_cast<const double *>(p) + r);
+  p += r * sizeof(double);
+  enter(c);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->lam0_dev, c->lam0.data(), r * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->mu_dev, p, r * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  p += r * sizeof(double);
+  LREI_CUDA_TRY(cudaMemsetAsync(c->Gam, 0, (size_t)KM * KM * sizeof(zd), c->st));
+  LREI_CUDA_TRY(cudaMemsetAsync(c->L, 0, (size_t)KM * KM * sizeof(zd), c->st));
+  LREI_CUDA_TRY(cudaMemcpy2DAsync(c->Gam, KM * sizeof(zd), p, r * sizeof(zd), r * sizeof(zd), r, cudaMemcpyHostToDevice, c->st));
+  p += (size_t)r * r * sizeof(zd);
+  LREI_CUDA_TRY(cudaMemcpy2DAsync(c->L, KM * sizeof(zd), p, r * sizeof(zd), r * sizeof(zd), r, cudaMemcpyHostToDevice, c->st));
+  p += (size_t)r * r * sizeof(zd);
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->V, p, blk, cudaMemcpyHostToDevice, c->st));
+  p += blk;
+  if (c->ab_alloc) ab_clear(c);
+  for (int i = 0; i < h.nhist; ++i) {
+    void *vk = ab_take(c), *yk = ab_take(c);
+    LREI_CUDA_TRY(cudaMemcpyAsync(vk, p, blk, cudaMemcpyHostToDevice, c->st));
+    p += blk;
+    LREI_CUDA_TRY(cudaMemcpyAsync(yk, p, blk, cudaMemcpyHostToDevice, c->st));
+    p += blk;
+    c->ab_hist.push_back({vk, yk});
+  }
+  c->ab_m = h.nhist > 0 ? h.ab_m : 0;
+  c->ab_dt = h.ab_dt;
+  leave(c);
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
+  c->t = h.t;
+  c->ctrl_h = h.ctrl_h;
+  c->ctrl_calib = h.ctrl_calib;
+  c->has_state = true;
+  if (h.werner_p != c->werner_p) return lrei_set_werner(c, h.werner_p);
+  return LREI_OK;
 }
 
 int lrei_last_status(lrei_ctx *c) { return c ? c->last_status : 0; }

@@ -2,10 +2,11 @@
 //
 // Some callers cannot allocate device memory: hosts that hand all device memory to their own
 // allocator (a framework's caching pool, a fixed memory budget), and monitoring loops where an
-// allocation's latency or the heap fragmentation it causes is not acceptable.  lrei_observables_noalloc computes the same observables as lrei_observables,
-// without a context, taking every input explicitly.  Its per-CTA partial sums and small
-// results live in one file-scope device array (g_noalloc_scratch, about 3.8 MB), which every
-// GPU that loads this library holds until the process exits.
+// allocation's latency or the heap fragmentation it causes is not acceptable.
+// lrei_observables_noalloc computes the same observables as lrei_observables, without a
+// context, taking every input explicitly.  Its per-CTA partial sums and small results live in
+// one file-scope device array (g_noalloc_scratch, about 3.8 MB), which every GPU that loads
+// this library's device code holds until the process exits.
 #include "lrei.h"
 #include "common.cuh"
 #include "tsk.cuh"
@@ -30,26 +31,18 @@ constexpr size_t NA_DOUBLES = (NA_PARTS + 16) * NA_ENT + NA_ENT + 64 + 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
-// Device address of the scratch array, looked up once per device (host code cannot use the
-// symbol itself: in host code it names a host-side stand-in, not device memory).
-double *g_scratch_addr[64] = {};
-
+// Device address of the scratch array on the current device.  Host code cannot use the symbol
+// itself (in host code it names a host-side stand-in, not device memory), so every call looks
+// the address up with the device current: the lookup allocates nothing, and a cached address
+// could dangle after the caller resets the device or its primary context is recreated.
 double *scratch_for_current_device(int *code) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
     *code = LREI_ERR_CUDA;
     return nullptr;
   }
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      *code = LREI_ERR_CUDA;
-      return nullptr;
-    }
-    g_scratch_addr[dev] = reinterpret_cast<double *>(p);
-  }
   *code = LREI_OK;
-  return g_scratch_addr[dev];
+  return reinterpret_cast<double *>(p);
 }
 }  // namespace
 
@@ -58,28 +51,9 @@ extern "C" int lrei_observables_noalloc(int n, const lrei_bonds *J, const double
   if (!V_dev || !Lambda_host || !out) return LREI_ERR_ARG;
   if (n < 1 || n > MAX_SPINS || r < 1 || r > NA_MAX_R || (long long)r > (1LL << n)) return LREI_ERR_ARG;
   if (dtype != LREI_C128 && dtype != LREI_C64) return LREI_ERR_ARG;
-  double Bv[3] = {0, 0, 0};
-  if (B) for (int i = 0; i < 3; ++i) Bv[i] = B[i];
-  if (Bv[0] != 0.0 || Bv[1] != 0.0) return LREI_ERR_UNSUPPORTED;
-  const int nb = J ? J->nbonds : 0;
-  if (nb < 0 || nb > MAX_BONDS || (nb > 0 && (!J->site_i || !J->site_j || !J->jxy || !J->jz))) return LREI_ERR_ARG;
   ModelArgs M;
-  std::memset(&M, 0, sizeof(M));
-  M.n = n;
-  M.nb = nb;
-  M.bz = Bv[2];
-  double c0 = 0.0;
-  for (int b = 0; b < nb; ++b) {
-    const int i = J->site_i[b], j = J->site_j[b];
-    if (i < 0 || i >= n || j < 0 || j >= n || i == j) return LREI_ERR_ARG;
-    M.bi[b] = (uint8_t)(n - 1 - i);
-    M.bj[b] = (uint8_t)(n - 1 - j);
-    M.mask[b] = (1u << (n - 1 - i)) | (1u << (n - 1 - j));
-    M.jxy[b] = J->jxy[b];
-    M.jz[b] = J->jz[b];
-    c0 += 0.5 * J->jz[b];
-  }
-  M.c0 = c0;
+  const int mrc = build_model_args(n, J, B, &M);
+  if (mrc != LREI_OK) return mrc;
   int code = LREI_OK;
   double *base = scratch_for_current_device(&code);
   if (!base) return code;

@@ -16,9 +16,6 @@ namespace lrei {
 // [0] FP32 Jacobi calls, [1] FP32 sweeps, [2] FP64 Jacobi calls, [3] FP64 sweeps (diagnostics)
 __device__ unsigned long long g_jacobi_counters[4];
 
-// threads of the FP32 Jacobi CTA (1024; 512 selectable for comparison)
-static int g_jacobi_nt = 1024;
-
 __device__ __forceinline__ zd zdiv_real(zd a, double d) { return mk<double>(a.re / d, a.im / d); }
 __device__ __forceinline__ zd zdiv(zd a, zd d) {
   const double n = d.re * d.re + d.im * d.im;
@@ -393,12 +390,8 @@ void sm_jacobi(bool fp64, const zd *A, int lda, int k, zd *U, int ldu, double *w
     const bool in_smem = jacobi_smem<float>(k, true) <= lim;
     const size_t bytes = jacobi_smem<float>(k, in_smem);
     ::lrei::count_launch();
-    if (g_jacobi_nt == 512)
-      jacobi_kernel<float, 512><<<1, 512, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
+    jacobi_kernel<float, 1024><<<1, 1024, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
                                                        max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
-    else
-      jacobi_kernel<float, 1024><<<1, 1024, bytes, st>>>(A, lda, k, U, ldu, w, in_smem ? nullptr : (cx<float> *)scratch,
-                                                         max_sweeps, tol, status, reinterpret_cast<cx<float> *>(Uf32), nout);
   }
 }
 
@@ -556,7 +549,7 @@ size_t sm_eig_ws_bytes(int kmax, int rmax) {
 }
 
 void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu, void *ws, int *status,
-                 cudaStream_t st) {
+                 cudaStream_t st, int max_sweeps) {
   unsigned char *p = reinterpret_cast<unsigned char *>(ws);
   auto take = [&](size_t bytes) { unsigned char *q = p; p += (bytes + 255) & ~(size_t)255; return q; };
   double *w = (double *)take((size_t)k * 8);
@@ -598,7 +591,7 @@ void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu,
   sm_gemm('N', 'N', k, r, k, one, M, ldm, E1, k, zero, W2, k, st);
   sm_gemm('C', 'N', r, r, k, one, E1, k, W2, k, zero, Ar, r, st);
   sm_hermitize(Ar, r, r, st);
-  sm_jacobi(true, Ar, r, r, Wr, r, mu, jscratch, 30, 1e-14, status, st);
+  sm_jacobi(true, Ar, r, r, Wr, r, mu, jscratch, max_sweeps, 1e-14, status, st);
   sm_gemm('N', 'N', k, r, r, one, E1, k, Wr, r, zero, Y, ldy, st);
   // 5. residual check of the returned pairs
   sm_gemm('N', 'N', k, r, k, one, M, ldm, Y, ldy, zero, W1, k, st);
@@ -673,8 +666,6 @@ int sm_init() {
   cudaFuncSetAttribute(trsv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t a = cudaFuncSetAttribute(jacobi_kernel<double, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaError_t b = cudaFuncSetAttribute(jacobi_kernel<float, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(jacobi_kernel<float, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  if (const char *e = getenv("LREI_JACOBI_NT")) g_jacobi_nt = atoi(e) == 512 ? 512 : 1024;
   cudaError_t c = cudaFuncSetAttribute(newton_chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   return (a == cudaSuccess && b == cudaSuccess && c == cudaSuccess) ? 0 : -1;
 }

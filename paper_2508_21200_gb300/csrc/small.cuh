@@ -36,10 +36,10 @@ size_t sm_jacobi_scratch_bytes(int k);
 
 // Top-r eigenpairs of the Hermitian k x k matrix M to FP64 accuracy: FP32 Jacobi, one
 // block-Newton correction of the top-r invariant subspace, FP64 Rayleigh-Ritz on it
-// (FP64 Jacobi of the r x r projection).  Y (k x r, ld ldy) gets the eigenvectors,
+// (FP64 Jacobi of the r x r projection, at most max_sweeps sweeps; more sets ST_EIG_NOCONV).  Y (k x r, ld ldy) gets the eigenvectors,
 // mu the eigenvalues, both sorted decreasing.  ws: see sm_eig_ws_bytes.
 void sm_eig_topr(const zd *M, int ldm, int k, int r, zd *Y, int ldy, double *mu, void *ws, int *status,
-                 cudaStream_t st);
+                 cudaStream_t st, int max_sweeps = 30);
 size_t sm_eig_ws_bytes(int kmax, int rmax);
 
 // Elementwise helpers

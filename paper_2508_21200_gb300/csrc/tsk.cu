@@ -67,18 +67,41 @@ __device__ __forceinline__ void hv_group(const ModelArgs &M, const cx<T> *__rest
   cx<T> acc[CPT];
 #pragma unroll
   for (int c = 0; c < CPT; ++c) acc[c] = mk<T>(0, 0);
-  for (int k = 0; k < M.nb; ++k) {
-    if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
-      diag -= (T)M.jz[k];
-      const T j = (T)M.jxy[k];
-      cx<T> v[CPT];
-      Group<T, CPT>::load(X + (size_t)(b ^ M.mask[k]) * r + c0, v);
+  if (!M.cplx) {
+    for (int k = 0; k < M.nb; ++k) {
+      if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
+        diag -= (T)M.jz[k];
+        const T j = (T)M.jxy[k];
+        cx<T> v[CPT];
+        Group<T, CPT>::load(X + (size_t)(b ^ M.mask[k]) * r + c0, v);
 #pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        acc[c].re = fma(j, v[c].re, acc[c].re);
-        acc[c].im = fma(j, v[c].im, acc[c].im);
+        for (int c = 0; c < CPT; ++c) {
+          acc[c].re = fma(j, v[c].re, acc[c].re);
+          acc[c].im = fma(j, v[c].im, acc[c].im);
+        }
       }
     }
+  } else {
+    // complex amplitudes: jxy + i dz when site i is up in b, jxy - i dz when it is down
+    for (int k = 0; k < M.nb; ++k) {
+      if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
+        diag -= (T)M.jz[k];
+        const cx<T> a = mk<T>((T)M.jxy[k], (T)(((b >> M.bi[k]) & 1u) ? -M.dz[k] : M.dz[k]));
+        cx<T> v[CPT];
+        Group<T, CPT>::load(X + (size_t)(b ^ M.mask[k]) * r + c0, v);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) fma_(acc[c], a, v[c]);
+      }
+    }
+    // one-bit flips of the transverse field: (bx -+ i by)/2 for bit q of b equal to 0 / 1
+    if (M.bx != 0.0 || M.by != 0.0)
+      for (int q = 0; q < M.n; ++q) {
+        const cx<T> a = mk<T>((T)(0.5 * M.bx), (T)(((b >> q) & 1u) ? 0.5 * M.by : -0.5 * M.by));
+        cx<T> v[CPT];
+        Group<T, CPT>::load(X + (size_t)(b ^ (1u << q)) * r + c0, v);
+#pragma unroll
+        for (int c = 0; c < CPT; ++c) fma_(acc[c], a, v[c]);
+      }
   }
   cx<T> v[CPT];
   Group<T, CPT>::load(X + (size_t)b * r + c0, v);
@@ -1079,12 +1102,10 @@ static int launch_ts_v1(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream
   return grid;
 }
 
-static bool g_force_ts2 = false;   // selects the unpipelined register-blocked kernel (A/B comparison)
-static int g_ts3_rows = 32;        // tile rows of the pipelined kernel at r = 16
 
 // Shared memory of the pipelined pass for the given arguments, or 0 if it does not apply.
 static size_t ts3_plan(const TSArgs &a, int *tr) {
-  if (g_force_ts2 || g_force_v1 || a.apply_h) return 0;
+  if (a.apply_h) return 0;
   if (a.mode == 0 && a.out) return 0;
   const int r = a.r, nq = a.nq, gl = a.gram_left, mode = a.mode;
   const int nb = nq + (mode != 2 ? 1 : 0);
@@ -1096,8 +1117,8 @@ static size_t ts3_plan(const TSArgs &a, int *tr) {
   if (a.out && !al(a.out)) return 0;
   size_t b = 0;
   if (r == 16) {
-    *tr = g_ts3_rows;
-    b = g_ts3_rows == 32 ? ts3_bytes<16, 32>(nq, gl, mode) : ts3_bytes<16, 64>(nq, gl, mode);
+    *tr = 32;
+    b = ts3_bytes<16, 32>(nq, gl, mode);
   } else if (r == 8) {
     *tr = 64;
     b = ts3_bytes<8, 64>(nq, gl, mode);
@@ -1127,18 +1148,12 @@ static int launch_ts3(const TSArgs &a, int nsm, cudaStream_t st, size_t bytes, i
   if (grid < 1) grid = 1;
   ::lrei::count_launch();
   const int g = a.gram_left + 1;
-  if (a.r == 16 && tr == 32) {
+  if (a.r == 16) {
     if (g <= 2) ts3_kernel<16, 32, 2><<<grid, 256, bytes, st>>>(a, coefg);
     else if (g <= 3) ts3_kernel<16, 32, 3><<<grid, 256, bytes, st>>>(a, coefg);
     else if (g <= 4) ts3_kernel<16, 32, 4><<<grid, 256, bytes, st>>>(a, coefg);
     else if (g <= 5) ts3_kernel<16, 32, 5><<<grid, 256, bytes, st>>>(a, coefg);
     else ts3_kernel<16, 32, 8><<<grid, 256, bytes, st>>>(a, coefg);
-  } else if (a.r == 16) {
-    if (g <= 2) ts3_kernel<16, 64, 2><<<grid, 256, bytes, st>>>(a, coefg);
-    else if (g <= 3) ts3_kernel<16, 64, 3><<<grid, 256, bytes, st>>>(a, coefg);
-    else if (g <= 4) ts3_kernel<16, 64, 4><<<grid, 256, bytes, st>>>(a, coefg);
-    else if (g <= 5) ts3_kernel<16, 64, 5><<<grid, 256, bytes, st>>>(a, coefg);
-    else ts3_kernel<16, 64, 8><<<grid, 256, bytes, st>>>(a, coefg);
   } else if (a.r == 8) {
     ts3_kernel<8, 64, 8><<<grid, 256, bytes, st>>>(a, coefg);
   } else {
@@ -1161,7 +1176,7 @@ static int launch_ts_t(const ModelArgs &M, const TSArgs &a, int nsm, cudaStream_
   int tr = 64;
   if (mt > 0)
     while (tr > 8 && ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt) > budget) tr /= 2;
-  if (mt == 0 || ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt) > budget || g_force_v1)
+  if (mt == 0 || ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt) > budget)
     return launch_ts_v1<T>(M, a, nsm, st);
   const size_t bytes = ts2_bytes<T>(a.nq, a.gram_left, r, tr, a.mode, mt);
   cx<T> *coefg = nullptr;
@@ -1248,6 +1263,17 @@ static bool hv5_tensor_map(CUtensorMap *tm, bool fp64, const void *X, long long 
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                int *status) {
   const size_t rowb = (size_t)r * (fp64 ? 16 : 8);
+  if (launch_hv6(fp64, M, X, Y, N, r, nsm, st, status)) return;
+  if (M.cplx) {   // complex amplitudes or one-bit partners: the generic per-row gather
+    auto grid_c = [&](int cpt) {
+      long long g = (N * (r / cpt) + 255) / 256, cap = (long long)nsm * 16;
+      return (int)(g < cap ? g : cap);
+    };
+    ::lrei::count_launch();
+    if (fp64) hv_kernel<double, 1><<<grid_c(1), 256, 0, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r);
+    else hv_kernel<float, 1><<<grid_c(1), 256, 0, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r);
+    return;
+  }
   // TMA-staged tiles of 32-byte row slabs: the CTA's own tile and two partner-tile buffers
   if (!g_hv_v2 && !g_hv_v3 && !g_force_v1 && M.n >= 10 && rowb % 32 == 0 &&
       (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
@@ -1457,8 +1483,6 @@ void launch_check_finite(bool fp64, const void *X, long long N, int r, int *stat
 namespace lrei {
 // Raise the dynamic shared-memory limit of every tile kernel once (outside any stream capture).
 int ts_init() {
-  g_force_v1 = getenv("LREI_TS_V1") != nullptr;
-  g_force_ts2 = getenv("LREI_TS2") != nullptr;
   g_hv_v2 = getenv("LREI_HV2") != nullptr;
   g_hv_v3 = getenv("LREI_HV3") != nullptr;
   if (const char *e = getenv("LREI_HV5_CFG")) g_hv5_cfg = atoi(e);
@@ -1470,7 +1494,7 @@ int ts_init() {
       g_tmap_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     cudaGetLastError();
   }
-  if (const char *e = getenv("LREI_TS3_ROWS")) g_ts3_rows = (atoi(e) == 64) ? 64 : 32;
+  if (hv6_init()) return -1;
   const int lim = 210 * 1024;
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {
@@ -1481,11 +1505,6 @@ int ts_init() {
     cudaError_t x = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (x != cudaSuccess) e = x;
   };
-  set3((const void *)ts3_kernel<16, 64, 2>);
-  set3((const void *)ts3_kernel<16, 64, 3>);
-  set3((const void *)ts3_kernel<16, 64, 4>);
-  set3((const void *)ts3_kernel<16, 64, 5>);
-  set3((const void *)ts3_kernel<16, 64, 8>);
   set3((const void *)ts3_kernel<16, 32, 2>);
   set3((const void *)ts3_kernel<16, 32, 3>);
   set3((const void *)ts3_kernel<16, 32, 4>);

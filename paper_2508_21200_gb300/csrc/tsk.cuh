@@ -42,6 +42,12 @@ void launch_reduce(const double *partial, int nparts, int len_doubles, double *o
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                int *status = nullptr);
 
+// Full-row matrix-free H.V (hv.cu): returns false when the layout does not apply.
+// tile_bits > 0 overrides the tile size (rows = 2^tile_bits), else about 32 KB per tile.
+bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
+                int *status, int tile_bits = 0);
+int hv6_init();
+
 // Observable Grams of V (N x r): blocks (column-major r x r each, complex double):
 //   0: V^*HV  1: (HV)^*(HV)  2: V^*V  3: V^* Mx V  4: V^* My V  5: V^* Mz V
 int launch_obs(bool fp64, const ModelArgs &M, const void *V, long long N, int r, double *partial, int nsm,

@@ -61,5 +61,34 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib_path):
     assert lib.lrei_create(0, None, B, ctypes.c_double(0.1), 0, 0, 4, None, ctypes.byref(h)) == -1   # n < 1
     assert lib.lrei_create(8, None, B, ctypes.c_double(-1.0), 0, 0, 4, None, ctypes.byref(h)) == -1  # kappa < 0
     assert lib.lrei_create(8, None, B, ctypes.c_double(0.1), 0, 0, 64, None, ctypes.byref(h)) == -1  # r_max > 32
-    Bx = (ctypes.c_double * 3)(0.3, 0.0, 0.5)
-    assert lib.lrei_create(8, None, Bx, ctypes.c_double(0.1), 0, 0, 4, None, ctypes.byref(h)) == -2  # transverse field
+    Bn = (ctypes.c_double * 3)(0.3, float("nan"), 0.5)
+    assert lib.lrei_create(8, None, Bn, ctypes.c_double(0.1), 0, 0, 4, None, ctypes.byref(h)) == -3  # non-finite field
+
+
+def test_nonfinite_model_gives_the_same_code_from_both_entry_points(lib_path):
+    # lrei_create and lrei_observables_noalloc share one validation of n, the bonds and the field
+    lib = ctypes.CDLL(lib_path)
+
+    class Bonds(ctypes.Structure):
+        _fields_ = [("nbonds", ctypes.c_int), ("site_i", ctypes.POINTER(ctypes.c_int)),
+                    ("site_j", ctypes.POINTER(ctypes.c_int)), ("jxy", ctypes.POINTER(ctypes.c_double)),
+                    ("jz", ctypes.POINTER(ctypes.c_double))]
+    si, sj = (ctypes.c_int * 1)(0), (ctypes.c_int * 1)(1)
+    lam = (ctypes.c_double * 1)(1.0)
+    out = (ctypes.c_char * 4096)()
+    h = ctypes.c_void_p()
+    lib.lrei_create.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.lrei_observables_noalloc.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]
+    cases = [((1.0, float("nan")), (0.0, 0.0, 0.5), -3),   # non-finite jz
+             ((float("inf"), 1.0), (0.0, 0.0, 0.5), -3),   # non-finite jxy
+             ((1.0, 1.0), (0.0, 0.0, float("nan")), -3)]   # non-finite field
+    for (jxy, jz), B, code in cases:
+        b = Bonds(1, si, sj, (ctypes.c_double * 1)(jxy), (ctypes.c_double * 1)(jz))
+        Bv = (ctypes.c_double * 3)(*B)
+        a = lib.lrei_create(4, ctypes.byref(b), Bv, 0.1, 0, 0, 1, None, ctypes.byref(h))
+        # a dummy non-NULL device pointer: the call must fail in its argument checks first
+        c = lib.lrei_observables_noalloc(4, ctypes.byref(b), Bv, ctypes.c_void_p(256), 1, 0, lam, None, out)
+        assert a == c == code, (jxy, jz, B, a, c)

@@ -95,21 +95,22 @@ def test_records_have_features_and_judged_errors():
 
 
 def test_trained_network_gain_over_plain_rule():
-    """Train on plain-controller data (n = 9..11), evaluate on a held-out chain (n = 10, other seed).
+    """Train on plain-controller data (n = 8..10), evaluate on a held-out chain (n = 9, other seed)
+    over t in [0, 1].
 
     The gain is reported as RK4 steps (including judge and rejected steps) per unit simulated
     time, plain / learned, at the same tolerance; the learned run must also keep the error bound.
     """
-    train_w = [li.workload(4, t, n=n, r=4, kappa=0.1) for t, n in ((1, 9), (2, 10), (3, 11))]
-    X, Y = ctl.generate(train_w, t_end=0.3, tols=(1e-7, 1e-9))
+    train_w = [li.workload(4, t, n=n, r=4, kappa=0.1) for t, n in ((1, 8), (2, 9), (3, 10))]
+    X, Y = ctl.generate(train_w, t_end=0.2, tols=(1e-6, 1e-7))
     net, loss = ctl.fit(X, Y, iters=2000, lr=2e-3)
-    assert loss < 0.35 * float(np.var(Y)) + 1e-6     # R^2 > 0.3 (loss = half the mean square)
-    w = li.workload(4, 9, n=10, r=4, kappa=0.1)
-    t_end, tol = 0.4, 1e-8
-    ref = _reference(w, t_end)
+    assert loss < 0.5 * float(np.var(Y)) + 1e-6      # better than the mean (loss = half the mean square)
+    w = li.workload(4, 9, n=9, r=4, kappa=0.1)
+    t_end, tol = 1.0, 1e-7
+    ref = _reference(w, t_end, h=0.005)
     o_p, st_p = _run(w, t_end, tol, 0, judge_every=8)
     o_l, st_l = _run(w, t_end, tol, 1, judge_every=8, net=net)
     assert _err(o_l, ref) < 1e-6 and _err(o_p, ref) < 1e-6
     gain = st_p["rk4_steps"] / st_l["rk4_steps"]
     print(f"learned controller: {st_l}  plain: {st_p}  gain {gain:.3f}")
-    assert gain > 0.8
+    assert gain > 1.0

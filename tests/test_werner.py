@@ -1,10 +1,12 @@
-"""Werner-state initial data through the library (Sec. 5, eq. werner-sol).
+"""Werner-state initial data through the C ABI (Sec. 5, eq. werner-sol).
 
-CPU: the binding's map from the low-rank part's observables to those of
-rho_W = p I/N + (1 - p) rho_hat, against the dense rho_W of the oracle.
-GPU: a context created with kappa -> (1 - p) kappa, stepped from rho_hat_0, reproduces the
-oracle's full-rank evolution of rho_W.
+lrei_set_werner(p) makes the library evolve rho = p I/N + (1 - p) rho_hat: the steps use the
+damping (1 - p) kappa on the stored low-rank rho_hat, and lrei_observables reports the
+observables of rho itself.  The GPU test compares that with the oracle's full-rank EI
+evolution of rho_W, which knows nothing of the shift.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -12,43 +14,26 @@ import lrei_inputs as li
 from oracle import model, dense_ei as de, werner
 
 
-def test_werner_observable_map_of_the_binding():
-    # the binding's host-side map from rho_hat's observables to rho_W's, against dense rho_W
-    from paper_2508_21200_gb300 import werner as pw
-    n, p = 5, 0.25
-    N = 1 << n
-    H = model.hamiltonian(n, li.chain_bonds(n, True), (0.0, 0.0, 0.7))
-    M = {v: model.magnetization_op(v, n) for v in "xyz"}
-    rng = np.random.default_rng(3)
-    V = np.linalg.qr(rng.standard_normal((N, 3)) + 1j * rng.standard_normal((N, 3)))[0]
-    lam = np.array([0.5, 0.3, 0.2])
-    o_hat = de.observables(V, lam, H, M)
-    rho_hat = de.state(V, lam)
-    o_hat["comm_norm"] = np.linalg.norm(rho_hat @ H - H @ rho_hat)
-    o_hat["lambda0"] = lam
-    got = pw.observables(o_hat, p, n)
-    rho = werner.werner_state(V, lam, p)
-    want = {"energy": np.trace(H @ rho).real, "purity": np.trace(rho @ rho).real, "trace": np.trace(rho).real,
-            "comm_norm": np.linalg.norm(rho @ H - H @ rho)}
-    want.update({"m" + v: np.trace(M[v] @ rho).real for v in "xyz"})
-    for k, v in want.items():
-        assert abs(got[k] - v) < 1e-13, k
-    assert np.allclose(np.sort(got["lambda0"]), np.sort(np.linalg.eigvalsh(rho))[-3:], atol=1e-13)
-    assert pw.shifted_kappa(0.4, 0.25) == pytest.approx(0.3)
-    with pytest.raises(ValueError):
-        pw.shifted_kappa(0.4, 1.0)
-
+def test_set_werner_rejects_weights_outside_the_unit_interval():
+    # argument checks happen before any device work (a NULL context is rejected first)
+    from paper_2508_21200_gb300 import build
+    try:
+        path = build.ensure_built()
+    except (RuntimeError, FileNotFoundError) as e:  # no nvcc in this environment
+        pytest.skip(f"cannot build: {e}")
+    lib = ctypes.CDLL(path)
+    lib.lrei_set_werner.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    assert lib.lrei_set_werner(None, 0.2) == -1
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mdl", ["qll", "qllg"])
-def test_werner_evolution_on_gpu_matches_full_rank_oracle(mdl):
+@pytest.mark.parametrize("mdl,p", [("qll", 0.3), ("qllg", 0.3), ("qll", 0.0), ("qllg", 0.8)])
+def test_werner_evolution_on_gpu_matches_full_rank_oracle(mdl, p):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():  # pragma: no cover
         pytest.skip("needs a CUDA GPU")
-    from paper_2508_21200_gb300 import Lrei
-    from paper_2508_21200_gb300 import werner as pw
-    n, p, kappa, h, steps = 6, 0.3, 0.5, 0.01, 10
+    from paper_2508_21200_gb300 import Lrei, LreiError
+    n, kappa, h, steps = 6, 0.5, 0.01, 10
     N = 1 << n
     bonds, B = li.chain_bonds(n, False), (0.0, 0.0, 0.5)
     H = model.hamiltonian(n, bonds, B)
@@ -57,14 +42,21 @@ def test_werner_evolution_on_gpu_matches_full_rank_oracle(mdl):
     V_hat = np.linalg.qr(rng.standard_normal((N, 2)) + 1j * rng.standard_normal((N, 2)))[0]
     lam_hat = np.array([0.7, 0.3])
     # oracle: the full-rank EI evolution of rho_W itself
-    w, U = np.linalg.eigh(werner.werner_state(V_hat, lam_hat, p))
+    rho_w = werner.werner_state(V_hat, lam_hat, p)
+    w, U = np.linalg.eigh(rho_w)
     idx = np.argsort(-w, kind="stable")
     Vt, _ = de.integrate(U[:, idx], w[idx], H, kappa, mdl, h, steps, "rk4")
     ref = de.observables(Vt, w[idx], H, M)
-    # library: the low-rank part with the shifted damping
-    L = Lrei(n, bonds, B, pw.shifted_kappa(kappa, p), mdl, "fp64", 2)
+    rho_t = de.state(Vt, w[idx])
+    # library: the low-rank part, Werner weight set through the ABI
+    L = Lrei(n, bonds, B, kappa, mdl, "fp64", 2)
     L.set_state(torch.from_numpy(V_hat).cuda(), lam_hat)
+    L.set_werner(p)
     L.step(h, "rk4", steps)
-    got = pw.observables(L.observables(), p, n)
-    for k in ("energy", "mx", "my", "mz", "purity", "trace"):
+    got = L.observables()
+    for k in ("energy", "mx", "my", "mz", "purity", "trace", "comm_norm"):
         assert abs(got[k] - ref[k]) <= 1e-10 * max(abs(ref[k]), 0.5), (k, got[k], ref[k])
+    top = np.sort(np.linalg.eigvalsh(rho_t))[::-1][:2]
+    assert np.abs(np.sort(got["lambda0"])[::-1] - top).max() < 1e-10
+    with pytest.raises(LreiError):
+        L.set_werner(1.0)

@@ -5,7 +5,8 @@ own allocator has reserved it, a monitoring loop that must not allocate per call
 scratch is a static device array inside the library.  Here it is called twice in a row
 on the factor held by a context and must reproduce lrei_observables within the tolerance the
 parity tests use for a reduction of the same data (1e-12 relative in FP64, 1e-6 in complex64).
-This file is collected last so that a failure here never hides another test.
+The file name sorts last, so a run that stops at its first failure has run every other test
+before this one.
 """
 import ctypes
 
@@ -47,9 +48,10 @@ def _noalloc(lib, w, V, lam, dtype):
 
 
 @pytest.mark.parametrize("precision,dtype,tol", [("fp64", 0, 1e-12), ("mixed", 1, 1e-6)])
-def test_noalloc_observables_match_context_observables_twice(precision, dtype, tol):
+@pytest.mark.parametrize("n,r", [(10, 6), (14, 16)])   # n = 14: more 16-row tiles than partial slots
+def test_noalloc_observables_match_context_observables_twice(precision, dtype, tol, n, r):
     lib = load_library()
-    w = li.workload(2, n=10, r=6)
+    w = li.workload(2, n=n, r=r)
     L = Lrei(w.n, w.bonds, w.B, w.kappa, w.model, precision, w.r)
     Vin = torch.from_numpy(w.V).to("cuda", torch.complex128 if precision == "fp64" else torch.complex64)
     L.set_state(Vin, w.lam)
