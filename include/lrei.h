@@ -127,8 +127,8 @@ int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
  * rejection, h_new = h clip(0.9 (tol/err)^(1/5), 0.2, 5)); 1 = the learned controller (the
  * attached network estimates the local error from the step's features, scaled by a factor
  * refitted at every judge; judged every 4 judge_every steps, after a rejection, and when its
- * estimate exceeds tol; a judge that finds the error more than 3x above the estimate hands
- * control to the plain rule for 16 steps).  tol bounds the relative local
+ * estimate is far below the calibrated drift; a judge that finds the error more than 3x above
+ * the estimate hands control to the plain rule for 16 steps).  tol bounds the relative local
  * error per step; it is raised to the
  * rounding floor of the context's precision (LREI_TOL_FLOOR_FP64,
  * LREI_TOL_FLOOR_MIXED), below which the step-doubling estimate is noise.
@@ -243,6 +243,27 @@ int lrei_checkpoint_load(lrei_ctx *ctx, const void *buf_host, long long bytes);
  * needs more sweeps, or whose eigenpair residual stays above its tolerance, returns
  * LREI_ERR_EIG_NOCONV with status bit 2 or 32 set. */
 int lrei_set_eig_sweeps(lrei_ctx *ctx, int max_sweeps);
+
+/* ---- many trajectories side by side ------------------------------------ */
+/* A batch runs the RK4 steps of many contexts (trajectories of uneven n, r, kappa, model and
+ * precision, each with its state set) as one CUDA graph launch per step: the graph holds every
+ * context's captured step as a child graph with no edges between them, so the GPU runs the
+ * trajectories side by side.  The contexts stay owned by the caller, must outlive the batch,
+ * and must not be used from another thread while a batch call runs; changing a context's
+ * model (lrei_set_dmi, lrei_set_werner, lrei_set_eig_sweeps) or rank requires a new batch.
+ * All work runs on cuda_stream (may be NULL), ordered after each context's own stream. */
+typedef struct lrei_batch lrei_batch;
+int lrei_batch_create(int nctx, lrei_ctx *const *ctxs, void *cuda_stream, lrei_batch **out);
+/* Advance every trajectory of the batch by nsteps RK4 steps of size dt; syncs and returns the
+ * first failing trajectory's error code (each context's lrei_last_status has its own bits). */
+int lrei_batch_step(lrei_batch *b, double dt, int nsteps);
+/* Autotuner of the batch's launch shape: for SM shares nsm, nsm/2, nsm/4, ... (down to a few
+ * SMs), every trajectory's persistent grids are sized to that share, the batch graph is rebuilt
+ * and `steps` batch steps of size dt are timed; the fastest share is kept and written to
+ * *nsm_out with its time per batch step (ms) to *ms_out (either may be NULL).  The timed steps
+ * advance the trajectories (t included); set the states again to start over. */
+int lrei_batch_autotune(lrei_batch *b, double dt, int steps, int *nsm_out, double *ms_out);
+int lrei_batch_destroy(lrei_batch *b);
 
 /* Raw device status bits of the last step / set_state call (diagnostics):
  * 1 non-finite, 2 small eigensolver sweep limit, 4 rank-deficient factor,

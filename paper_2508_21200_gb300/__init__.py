@@ -15,7 +15,7 @@ import numpy as np
 
 from .build import LIB, ensure_built
 
-__all__ = ["Lrei", "LreiError", "load_library", "QLL", "QLLG", "FP64", "MIXED_C64", "SCHEMES"]
+__all__ = ["Lrei", "Batch", "LreiError", "load_library", "QLL", "QLLG", "FP64", "MIXED_C64", "SCHEMES"]
 
 QLL, QLLG = 0, 1
 FP64, MIXED_C64 = 0, 1
@@ -80,6 +80,10 @@ def load_library(path: str | None = None):
         "lrei_set_werner": (I, [P, D]),
         "lrei_set_dmi": (I, [P, I, ctypes.POINTER(D)]),
         "lrei_set_eig_sweeps": (I, [P, I]),
+        "lrei_batch_create": (I, [I, P, P, ctypes.POINTER(P)]),
+        "lrei_batch_step": (I, [P, D, I]),
+        "lrei_batch_autotune": (I, [P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+        "lrei_batch_destroy": (I, [P]),
         "lrei_checkpoint_bytes": (L, [P]),
         "lrei_checkpoint_save": (I, [P, P, L]),
         "lrei_checkpoint_load": (I, [P, P, L]),
@@ -315,6 +319,38 @@ class Lrei:
         if n.value:
             _check(self._lib.lrei_controller_records(self._h, rows.ctypes.data, n.value, ctypes.byref(n)))
         return rows
+
+
+class Batch:
+    """Many contexts stepped together: one graph launch per RK4 step of the whole batch."""
+
+    def __init__(self, contexts, stream=None):
+        self._lib = load_library()
+        self._ctx = list(contexts)          # the contexts must outlive the batch
+        arr = (ctypes.c_void_p * len(self._ctx))(*[c._h.value for c in self._ctx])
+        h = ctypes.c_void_p()
+        _check(self._lib.lrei_batch_create(len(self._ctx), arr, _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+
+    def step(self, dt, nsteps=1):
+        _check(self._lib.lrei_batch_step(self._h, float(dt), int(nsteps)))
+
+    def autotune(self, dt, steps=2):
+        """Pick the SM share per trajectory by timing batch steps; returns (share, ms per batch step)."""
+        k, ms = ctypes.c_int(), ctypes.c_double()
+        _check(self._lib.lrei_batch_autotune(self._h, float(dt), int(steps), ctypes.byref(k), ctypes.byref(ms)))
+        return k.value, ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lrei_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mlp:

@@ -739,8 +739,10 @@ struct lrei_ctx {
   double t = 0.0;
   double dt_cur = 0.0;
   bool has_state = false;
-  // graph cache for one step of a given scheme
+  // graph cache for one step of a given scheme (the captured graph and its instance)
+  cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  int nsm_use = 0;   // SMs the N-length passes spread over (all of them unless a batch shares the GPU)
   int g_scheme = -1, g_r = -1;
   long long g_nodes = 0;
   long long launches = 0, cnt0 = 0;
@@ -825,7 +827,7 @@ int ts_pass(lrei_ctx *c, TSArgs a, int nsm = 0) {
   a.r = c->r;
   a.partial = c->partial;
   a.coef_scratch = c->coef_scratch;
-  int g = launch_ts(c->fp64, c->M, a, nsm > 0 ? nsm : c->nsm, c->st);
+  int g = launch_ts(c->fp64, c->M, a, nsm > 0 ? nsm : c->nsm_use, c->st);
   if (g < 0) return LREI_ERR_ARG;
   launch_reduce(c->partial, g, (int)ts_partial_doubles(a.gram_left, c->r), c->red, c->st);
   return LREI_OK;
@@ -993,6 +995,10 @@ int build_graph(lrei_ctx *c, int scheme) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
   }
+  if (c->graph) {
+    cudaGraphDestroy(c->graph);
+    c->graph = nullptr;
+  }
   cudaGraph_t g = nullptr;
   const long long before = launch_counter();
   LREI_CUDA_TRY(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
@@ -1006,7 +1012,7 @@ int build_graph(lrei_ctx *c, int scheme) {
   if (e != cudaSuccess) return cuda_fail(e, "capture");
   c->g_nodes = count_kernel_nodes(g);
   e = cudaGraphInstantiate(&c->gexec, g, 0);
-  cudaGraphDestroy(g);
+  c->graph = g;   // kept: a batch of contexts runs it as a child graph
   if (e != cudaSuccess) return cuda_fail(e, "instantiate");
   c->g_scheme = scheme;
   c->g_r = c->r;
@@ -1227,8 +1233,8 @@ int enqueue_ab_step(lrei_ctx *c, int m) {
 // system size, another tolerance) is absorbed at the first judge and the network only has to
 // follow the variation between judges.  The same formula turns either estimate into the next h.
 // A judge that finds the error more than 3x above the corrected estimate hands control to the
-// plain rule for the next 16 steps; an estimate above tol, or more than 10x below the calibrated
-// drift, is judged before it is used.
+// plain rule for the next 16 steps; an estimate more than 10x below the calibrated drift is
+// judged before it is used.
 constexpr int NFEAT = 40;
 
 int ctrl_prepare(lrei_ctx *c) {
@@ -1373,9 +1379,8 @@ int run_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
     const double err_plain = (c->ctrl_calib > 0 ? c->ctrl_calib : 1.0) * drift;
     // the network's estimate times its correction factor (refitted at every judge)
     const double err_learn = err_net >= 0 ? (c->learn_corr > 0 ? c->learn_corr : 1.0) * err_net : -1.0;
-    // an estimate far below the calibrated drift, or above tol, is checked by a judge before it
-    // is used (a step is never rejected on the network's word alone)
-    const bool doubtful = learned && (err_learn < 0 || err_learn < 0.1 * err_plain || err_learn > tol);
+    // an estimate far below the calibrated drift is checked by a judge before it is used
+    const bool doubtful = learned && (err_learn < 0 || err_learn < 0.1 * err_plain);
     const bool do_judge = since_judge >= period || last_rejected || c->ctrl_calib < 0 || doubtful;
     double err;
     c->st_rk4 += 1;
@@ -1527,8 +1532,11 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
   cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   for (int i = 0; i < 4; ++i) cudaEventCreateWithFlags(&c->ev_kry[i], cudaEventDisableTiming);
-  // the N-length passes of the RK step leave one SM in sixteen to the stage algebra running beside them
-  c->nsm_pass = c->nsm - std::max(1, c->nsm / 16);
+  c->nsm_use = c->nsm;
+  // the complex64 N-length passes of the RK step leave one SM in sixteen to the stage algebra
+  // running beside them; the FP64 passes are long enough that the stage algebra hides behind
+  // them without a reserve
+  c->nsm_pass = c->fp64 ? c->nsm_use : c->nsm_use - std::max(1, c->nsm_use / 16);
   if (ts_init() || sm_init()) return fail(LREI_ERR_CUDA);
   {
     const int lim = 100 * 1024;
@@ -1590,6 +1598,7 @@ int lrei_destroy(lrei_ctx *c) {
   if (c->st) cudaStreamSynchronize(c->st);
   if (c->st2) cudaStreamSynchronize(c->st2);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
   for (void *p : c->allocs) cudaFree(p);
   if (c->status_host) cudaFreeHost(c->status_host);
   if (c->obs_host) cudaFreeHost(c->obs_host);
@@ -2262,6 +2271,163 @@ int lrei_checkpoint_load(lrei_ctx *c, const void *buf, long long bytes) {
   c->ctrl_calib = h.ctrl_calib;
   c->has_state = true;
   if (h.werner_p != c->werner_p) return lrei_set_werner(c, h.werner_p);
+  return LREI_OK;
+}
+
+// ---- many trajectories side by side: one graph launch per RK4 step of the whole batch
+struct lrei_batch {
+  std::vector<lrei_ctx *> ctx;
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double dt = 0.0;
+  int nsm_use = 0;
+};
+
+namespace {
+void set_sm_share(lrei_ctx *c, int nsm) {
+  nsm = std::max(1, std::min(nsm, c->nsm));
+  if (nsm == c->nsm_use) return;
+  c->nsm_use = nsm;
+  c->nsm_pass = c->fp64 ? nsm : std::max(1, nsm - (nsm >= 16 ? nsm / 16 : 0));
+  if (c->gexec) {   // grid sizes are baked into the captured step
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->g_scheme = -1;
+  }
+}
+
+int batch_build(lrei_batch *b) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  for (lrei_ctx *c : b->ctx) {
+    int rc = build_graph(c, (int)LREI_RK4);
+    if (rc) return rc;
+  }
+  LREI_CUDA_TRY(cudaGraphCreate(&b->graph, 0));
+  // independent child graphs: the trajectories have no edges between them
+  for (lrei_ctx *c : b->ctx) {
+    cudaGraphNode_t node;
+    LREI_CUDA_TRY(cudaGraphAddChildGraphNode(&node, b->graph, nullptr, 0, c->graph));
+  }
+  LREI_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+  return LREI_OK;
+}
+
+int batch_run(lrei_batch *b, double dt, int nsteps) {
+  // order the batch after the contexts' own streams
+  for (lrei_ctx *c : b->ctx) {
+    LREI_CUDA_TRY(cudaEventRecord(c->ev_out, c->st));
+    LREI_CUDA_TRY(cudaStreamWaitEvent(b->st, c->ev_out, 0));
+  }
+  if (dt != b->dt) {
+    for (lrei_ctx *c : b->ctx) {
+      LREI_CUDA_TRY(cudaMemcpy(c->dt_dev, &dt, sizeof(double), cudaMemcpyHostToDevice));
+      c->dt_cur = dt;
+    }
+    b->dt = dt;
+  }
+  for (int i = 0; i < nsteps; ++i) LREI_CUDA_TRY(cudaGraphLaunch(b->exec, b->st));
+  LREI_CUDA_TRY(cudaEventRecord(b->ev, b->st));
+  LREI_CUDA_TRY(cudaEventSynchronize(b->ev));
+  int code = LREI_OK;
+  for (lrei_ctx *c : b->ctx) {
+    LREI_CUDA_TRY(cudaStreamWaitEvent(c->st, b->ev, 0));
+    c->t += dt * nsteps;
+    c->launches += c->g_nodes * nsteps;
+    const int s = read_status(c);
+    if (s && code == LREI_OK) code = status_to_code(s);
+  }
+  return code;
+}
+}  // namespace
+
+int lrei_batch_create(int nctx, lrei_ctx *const *ctxs, void *cuda_stream, lrei_batch **out) {
+  if (!out || nctx < 1 || !ctxs) return LREI_ERR_ARG;
+  *out = nullptr;
+  int dev = -1;
+  for (int i = 0; i < nctx; ++i) {
+    if (!ctxs[i]) return LREI_ERR_ARG;
+    if (!ctxs[i]->has_state) return LREI_ERR_STATE;
+    if (dev < 0) dev = ctxs[i]->dev;
+    if (ctxs[i]->dev != dev) return LREI_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return LREI_ERR_ARG;
+  }
+  lrei_batch *b = new (std::nothrow) lrei_batch();
+  if (!b) return LREI_ERR_OOM;
+  b->ctx.assign(ctxs, ctxs + nctx);
+  b->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  b->nsm_use = ctxs[0]->nsm;
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return LREI_ERR_CUDA;
+  }
+  const int rc = batch_build(b);
+  if (rc) {
+    lrei_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return LREI_OK;
+}
+
+int lrei_batch_step(lrei_batch *b, double dt, int nsteps) {
+  if (!b || !std::isfinite(dt) || nsteps < 0) return LREI_ERR_ARG;
+  if (nsteps == 0) return LREI_OK;
+  return batch_run(b, dt, nsteps);
+}
+
+int lrei_batch_autotune(lrei_batch *b, double dt, int steps, int *nsm_out, double *ms_out) {
+  if (!b || !std::isfinite(dt) || steps < 1) return LREI_ERR_ARG;
+  const int nsm = b->ctx[0]->nsm;
+  int best = nsm;
+  double best_ms = 1e300;
+  cudaEvent_t e0, e1;
+  LREI_CUDA_TRY(cudaEventCreate(&e0));
+  LREI_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = LREI_OK;
+  for (int share = nsm; share >= 1 && !rc; share = (share > 1 ? share / 2 : 0)) {
+    for (lrei_ctx *c : b->ctx) set_sm_share(c, share);
+    if ((rc = batch_build(b))) break;
+    if ((rc = batch_run(b, dt, 1))) break;   // warm-up
+    cudaEventRecord(e0, b->st);
+    for (int i = 0; i < steps; ++i) cudaGraphLaunch(b->exec, b->st);
+    cudaEventRecord(e1, b->st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = LREI_ERR_CUDA; break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    for (lrei_ctx *c : b->ctx) {
+      c->t += dt * steps;
+      c->launches += c->g_nodes * steps;
+      const int s = read_status(c);
+      if (s && !rc) rc = status_to_code(s);
+    }
+    if (ms / steps < best_ms) {
+      best_ms = ms / steps;
+      best = share;
+    }
+    if (share < 8) break;   // candidates: nsm, nsm/2, ..., down to a few SMs per trajectory
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  for (lrei_ctx *c : b->ctx) set_sm_share(c, best);
+  b->nsm_use = best;
+  if ((rc = batch_build(b))) return rc;
+  if (nsm_out) *nsm_out = best;
+  if (ms_out) *ms_out = best_ms;
+  return LREI_OK;
+}
+
+int lrei_batch_destroy(lrei_batch *b) {
+  if (!b) return LREI_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev) cudaEventDestroy(b->ev);
+  delete b;
   return LREI_OK;
 }
 

@@ -23,8 +23,8 @@
 //    are in flight per thread;
 //  * straddling (one bit on each side): activity per row from one low bit and one tile bit;
 //    the partner row is loaded from global memory like an outside bond's.
-// Tiles are double-buffered: while a CTA computes one tile, the bulk copy of its next tile is
-// in flight.  Every wait on a copy is bounded; a wait that runs out sets ST_TIMEOUT, the tile
+// The own tile is single- or double-buffered (a template parameter; the library runs several
+// single-buffered CTAs per SM, which overlap each other's copies).  Every wait on a copy is bounded; a wait that runs out sets ST_TIMEOUT, the tile
 // is skipped, and before the kernel exits thread 0 waits (again bounded) for every copy it
 // issued, so no copy is left in flight into released shared memory.
 #include "common.cuh"
@@ -104,9 +104,11 @@ struct HvPlan {
 };
 
 // RPT: rows per thread and tile (tile bytes / 16 / 256 threads; 8 for the 32 KB tiles of the
-// launcher).  CPLX: complex amplitudes or one-bit terms present.
-template <typename T, int NBUF, int RPT, bool CPLX>
-__global__ void __launch_bounds__(256, 2) hv6_kernel(const __grid_constant__ HvPlan P,
+// launcher).  CPLX: complex amplitudes or one-bit terms present.  ROWMAJOR: each thread takes its
+// rows one at a time and issues the outside partner loads of a row LIF at a time; otherwise it
+// goes term by term over all its rows (RPT loads per term).  MINB: CTAs per SM to fit.
+template <typename T, int NBUF, int RPT, bool CPLX, bool ROWMAJOR, int LIF, int MINB>
+__global__ void __launch_bounds__(256, MINB) hv6_kernel(const __grid_constant__ HvPlan P,
                                                   const typename W16<T>::V *__restrict__ X,
                                                   typename W16<T>::V *__restrict__ Y, int *status) {
   using V = typename W16<T>::V;
@@ -225,7 +227,56 @@ __global__ void __launch_bounds__(256, 2) hv6_kernel(const __grid_constant__ HvP
       ok = false;
       break;
     }
-    if (slot < rp) {
+    if (ROWMAJOR && slot < rp) {
+      const V *own = buf + (size_t)b * TR * ch;
+      const int nf = nfa;
+      const T dc = dconst;
+      const unsigned long long sf = sflip, sg = ssel;
+      for (uint32_t lr = slot; lr < TR; lr += rp) {
+        const uint32_t row = t0 + lr;
+        T d = dc + rdiag[lr];
+        V acc = zero16((V *)nullptr);
+        // outside terms: LIF partner loads at a time, then their sums
+        for (int f0 = 0; f0 < nf; f0 += LIF) {
+          V p[LIF];
+#pragma unroll
+          for (int u = 0; u < LIF; ++u)
+            if (f0 + u < nf) p[u] = ld_stream(X + (size_t)(row ^ fmask[f0 + u]) * ch + c);
+#pragma unroll
+          for (int u = 0; u < LIF; ++u)
+            if (f0 + u < nf) {
+              if constexpr (CPLX) caxpy(acc, fr[f0 + u], fi[f0 + u], p[u]);
+              else axpy(acc, fr[f0 + u], p[u]);
+            }
+        }
+        for (int k = 0; k < nS; ++k)
+          if (((lr >> slo[k]) ^ (uint32_t)(sf >> k)) & 1u) {
+            d -= sjz[k];
+            const V pv = ld_stream(X + (size_t)(row ^ smask[k]) * ch + c);
+            if constexpr (CPLX) {
+              const bool s1 = sselin[k] ? ((lr >> ssb[k]) & 1u) : ((sg >> k) & 1u);
+              caxpy(acc, s1 ? s1r[k] : s0r[k], s1 ? s1i[k] : s0i[k], pv);
+            } else {
+              axpy(acc, s0r[k], pv);
+            }
+          }
+        unsigned long long am = rmask[lr];
+        while (am) {
+          const int k = __ffsll((long long)am) - 1;
+          am &= am - 1;
+          const V pv = own[(size_t)(lr ^ imask[k]) * ch + c];
+          if constexpr (CPLX) {
+            const bool s1 = (lr >> isb[k]) & 1u;
+            caxpy(acc, s1 ? i1r[k] : i0r[k], s1 ? i1i[k] : i0i[k], pv);
+          } else {
+            axpy(acc, i0r[k], pv);
+          }
+        }
+        axpy(acc, d, own[(size_t)lr * ch + c]);
+        __stcs(Y + (size_t)row * ch + c, acc);   // streaming: keep V, not Y, in L2
+      }
+    }
+    if (!ROWMAJOR && slot < rp) {
       const V *own = buf + (size_t)b * TR * ch;
       const int nf = nfa;
       const T dc = dconst;
@@ -286,7 +337,7 @@ __global__ void __launch_bounds__(256, 2) hv6_kernel(const __grid_constant__ HvP
           }
         }
         axpy(acc[i], d, own[(size_t)lr * ch + c]);
-        Y[(size_t)row * ch + c] = acc[i];
+        __stcs(Y + (size_t)row * ch + c, acc[i]);
       }
     }
     __syncthreads();   // buffer b and the per-tile lists are free again
@@ -305,15 +356,24 @@ __global__ void __launch_bounds__(256, 2) hv6_kernel(const __grid_constant__ HvP
 
 // ---------------------------------------------------------------- launcher
 constexpr int HV6_RPT = 8;   // rows per thread and tile at the launcher's tile sizes (see hv6_tile_bits)
+// the configuration the library launches (measured best of row/term order, 1-2 own-tile buffers,
+// 4-8 loads in flight and 2-6 CTAs per SM at n = 18 and 20): row-major, one own-tile buffer per
+// CTA (the 5 CTAs of an SM overlap each other's copies), 6 outside partner loads in flight per
+// thread, 5 CTAs per SM
+constexpr int HV6_NBUF = 1, HV6_LIF = 6, HV6_MINB = 5;
+constexpr bool HV6_ROWMAJOR = true;
 
-namespace {
-int g_hv6_occ[2] = {0, 0};   // [fp64]: CTAs per SM at the standard tile size
+template <typename T, bool CPLX>
+constexpr auto hv6_product = hv6_kernel<T, HV6_NBUF, HV6_RPT, CPLX, HV6_ROWMAJOR, HV6_LIF, HV6_MINB>;
 
 template <typename T>
-size_t hv6_smem_bytes(int tb, int ch) {
+size_t hv6_smem_bytes(int tb, int ch, int nbuf) {
   const size_t TR = (size_t)1 << tb;
-  return 2 * TR * ch * 16 + TR * (8 + sizeof(T));
+  return (size_t)nbuf * TR * ch * 16 + TR * (8 + sizeof(T));
 }
+
+namespace {
+int g_hv6_occ[2][2] = {{0, 0}, {0, 0}};   // [fp64][cplx]: CTAs per SM of the product kernel
 }  // namespace
 
 // Tile bits for a row of `rowb` bytes: about 32 KB of rows per tile, at most all N rows.
@@ -330,28 +390,30 @@ int hv6_init() {
     const cudaError_t x = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (x != cudaSuccess) e = x;
   };
-  set((const void *)hv6_kernel<float, 2, HV6_RPT, false>);
-  set((const void *)hv6_kernel<double, 2, HV6_RPT, false>);
-  set((const void *)hv6_kernel<float, 2, HV6_RPT, true>);
-  set((const void *)hv6_kernel<double, 2, HV6_RPT, true>);
+  set((const void *)hv6_product<float, false>);
+  set((const void *)hv6_product<double, false>);
+  set((const void *)hv6_product<float, true>);
+  set((const void *)hv6_product<double, true>);
   if (e != cudaSuccess) return -1;
   // occupancy at the standard tile size (32 KB per tile buffer)
   int o = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_kernel<float, 2, HV6_RPT, true>, 256, hv6_smem_bytes<float>(8, 8));
-  g_hv6_occ[0] = o > 0 ? o : 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_kernel<double, 2, HV6_RPT, true>, 256, hv6_smem_bytes<double>(7, 16));
-  g_hv6_occ[1] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<float, false>, 256, hv6_smem_bytes<float>(8, 8, HV6_NBUF));
+  g_hv6_occ[0][0] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<float, true>, 256, hv6_smem_bytes<float>(8, 8, HV6_NBUF));
+  g_hv6_occ[0][1] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<double, false>, 256, hv6_smem_bytes<double>(7, 16, HV6_NBUF));
+  g_hv6_occ[1][0] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<double, true>, 256, hv6_smem_bytes<double>(7, 16, HV6_NBUF));
+  g_hv6_occ[1][1] = o > 0 ? o : 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Returns true when the launch was made (row bytes a multiple of 16, aligned blocks, n large
-// enough for one 16-row tile, at most 64 terms inside a tile); false when the caller must use
-// another kernel.
-bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
-                int *status, int tile_bits) {
+// The terms of the model sorted for a tile size (tile_bits > 0 overrides the 32 KB default).
+// Returns false when hv6 does not apply: row bytes not a multiple of 16, fewer than 16 rows per
+// tile, or more than 64 terms inside a tile.
+bool hv6_plan(bool fp64, const ModelArgs &M, long long N, int r, int tile_bits, HvPlan *Pout) {
   const size_t rowb = (size_t)r * (fp64 ? 16 : 8);
   if (rowb % 16 != 0 || rowb / 16 > 256) return false;
-  if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Y) & 15) || X == Y) return false;
   int tb = tile_bits > 0 ? (tile_bits < M.n ? tile_bits : M.n) : hv6_tile_bits(M.n, rowb);
   const int rp = 256 / (int)(rowb / 16);
   while (tb > 0 && (((1 << tb) + rp - 1) / rp) > HV6_RPT) --tb;   // every row of a tile has a thread
@@ -359,7 +421,7 @@ bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long
   // the terms: the bonds, then (with a transverse field) one one-bit flip per spin
   const bool field = M.cplx && (M.bx != 0.0 || M.by != 0.0);
   const int nterm = M.nb + (field ? M.n : 0);
-  HvPlan P;
+  HvPlan &P = *Pout;
   std::memset(&P, 0, sizeof(P));
   P.N = N;
   P.n = M.n;
@@ -404,18 +466,27 @@ bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long
       P.a1i[q] = 0.5 * M.by;
     }
   }
-  const size_t smem = fp64 ? hv6_smem_bytes<double>(tb, P.ch) : hv6_smem_bytes<float>(tb, P.ch);
+  return true;
+}
+
+// Returns true when the launch was made; false when the caller must use another kernel.
+bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
+                int *status, int tile_bits) {
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Y) & 15) || X == Y) return false;
+  HvPlan P;
+  if (!hv6_plan(fp64, M, N, r, tile_bits, &P)) return false;
+  const size_t smem = fp64 ? hv6_smem_bytes<double>(P.tb, P.ch, HV6_NBUF) : hv6_smem_bytes<float>(P.tb, P.ch, HV6_NBUF);
   if (smem > 200 * 1024) return false;
-  const int occ = g_hv6_occ[fp64 ? 1 : 0];
-  const long long ntiles = N >> tb;
+  const int occ = g_hv6_occ[fp64 ? 1 : 0][M.cplx ? 1 : 0];
+  const long long ntiles = N >> P.tb;
   const long long cap = (long long)(occ > 0 ? occ : 1) * nsm;
   const int grid = (int)(ntiles < cap ? ntiles : cap);
   ::lrei::count_launch();
   if (fp64) {
-    auto kern = M.cplx ? hv6_kernel<double, 2, HV6_RPT, true> : hv6_kernel<double, 2, HV6_RPT, false>;
+    auto kern = M.cplx ? hv6_product<double, true> : hv6_product<double, false>;
     kern<<<grid, 256, smem, st>>>(P, reinterpret_cast<const double2 *>(X), reinterpret_cast<double2 *>(Y), status);
   } else {
-    auto kern = M.cplx ? hv6_kernel<float, 2, HV6_RPT, true> : hv6_kernel<float, 2, HV6_RPT, false>;
+    auto kern = M.cplx ? hv6_product<float, true> : hv6_product<float, false>;
     kern<<<grid, 256, smem, st>>>(P, reinterpret_cast<const float4 *>(X), reinterpret_cast<float4 *>(Y), status);
   }
   return true;

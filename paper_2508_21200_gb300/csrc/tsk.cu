@@ -1,9 +1,9 @@
 // Tall-skinny (N-length) kernels of the LREI hot path.
 //
-//  * Matrix-free H.V (paper Sec. 3.3: "sparsity of H"; Hamiltonian eq. H1):
-//    row b of Y = H V is diag(b) V[b] + sum over bonds whose two spins are
-//    antiparallel in b of jxy * V[b ^ mask], with mask the two bonds' bits.
-//    A thread owns CPT consecutive columns of one row; partner rows are read
+//  * The per-row matrix-free H.V gather (hv_group; paper Sec. 3.3 "sparsity of H",
+//    Hamiltonian eq. H1), used inside the fused passes and as the fallback of the
+//    full-row H.V kernel of hv.cu for rows that are not a multiple of 16 bytes:
+//    a thread owns CPT consecutive columns of one row; partner rows are read
 //    through the read-only cache (rows of one N x r block are contiguous).
 //  * Fused tile passes (apply / extend / combine, see tsk.cuh) compute the
 //    tall-skinny products Q^*S, S^*S, S A + Q C of the block-Krylov partial
@@ -15,9 +15,6 @@
 // accumulators that are FP64 (complex128 path) or compensated FP32 pairs
 // (complex64 path, TwoSum), written out as FP64 partials.
 #include "tsk.cuh"
-
-#include <cuda.h>
-#include <cudaTypedefs.h>
 
 #include <cstdlib>
 
@@ -129,335 +126,6 @@ __global__ void __launch_bounds__(256) hv_kernel(const __grid_constant__ ModelAr
   }
 }
 
-// ------------------------------------------------ H.V, slab-major with shared-memory tiles
-// The N x r block is processed in column slabs of 32 bytes per row (4 complex64 or 2 complex128
-// columns), slab by slab (CTA index = slab * tiles + tile), so while one slab is being
-// processed its rows (N * 32 B: 32 MB at N = 2^20) stay resident in L2 and the bit-flip partner
-// rows of bonds that leave a tile are L2 hits.  A CTA stages a tile of TR = 2^t consecutive rows
-// of its slab in shared memory: bonds whose two bits are both below t find their partner in the
-// tile; the others read it from global memory (L2).
-template <typename T>
-__global__ void __launch_bounds__(256) hv2_kernel(const __grid_constant__ ModelArgs M, const cx<T> *__restrict__ X,
-                                                  cx<T> *__restrict__ Y, long long N, int r, int tbits) {
-  constexpr int SW = 32 / sizeof(cx<T>);   // complex elements per slab row
-  extern __shared__ __align__(16) unsigned char smem_hv[];
-  cx<T> *tile = reinterpret_cast<cx<T> *>(smem_hv);   // TR x SW
-  const long long TR = 1LL << tbits;
-  const long long ntile = (N + TR - 1) / TR;
-  const int slab = (int)(blockIdx.x / ntile);
-  const long long t0 = (blockIdx.x % ntile) * TR;
-  const int c0 = slab * SW;
-  const int rows = (int)((N - t0) < TR ? (N - t0) : TR);
-  // stage the tile (16-byte vectors; SW * sizeof(cx<T>) = 32 bytes per row)
-  for (int e = threadIdx.x; e < rows * 2; e += blockDim.x) {
-    const int lr = e >> 1, half = e & 1;
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(X + (size_t)(t0 + lr) * r + c0) + half);
-    reinterpret_cast<float4 *>(tile + (size_t)lr * SW)[half] = v;
-  }
-  __syncthreads();
-  for (int lr = threadIdx.x; lr < rows; lr += blockDim.x) {
-    const uint32_t b = (uint32_t)(t0 + lr);
-    T diag = (T)(M.c0 + M.bz * (0.5 * M.n - (double)__popc(b)));
-    cx<T> acc[SW];
-#pragma unroll
-    for (int c = 0; c < SW; ++c) acc[c] = mk<T>(0, 0);
-    for (int k = 0; k < M.nb; ++k) {
-      if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
-        diag -= (T)M.jz[k];
-        const T j = (T)M.jxy[k];
-        const uint32_t pb = b ^ M.mask[k];
-        cx<T> v[SW];
-        if ((long long)M.mask[k] < TR) {
-          const cx<T> *p = tile + (size_t)(pb - (uint32_t)t0) * SW;
-#pragma unroll
-          for (int c = 0; c < SW; ++c) v[c] = p[c];
-        } else {
-          const float4 *p = reinterpret_cast<const float4 *>(X + (size_t)pb * r + c0);
-          float4 q0 = __ldg(p), q1 = __ldg(p + 1);
-          const cx<T> *qq0 = reinterpret_cast<const cx<T> *>(&q0);
-          const cx<T> *qq1 = reinterpret_cast<const cx<T> *>(&q1);
-#pragma unroll
-          for (int c = 0; c < SW / 2; ++c) { v[c] = qq0[c]; v[SW / 2 + c] = qq1[c]; }
-        }
-#pragma unroll
-        for (int c = 0; c < SW; ++c) {
-          acc[c].re = fma(j, v[c].re, acc[c].re);
-          acc[c].im = fma(j, v[c].im, acc[c].im);
-        }
-      }
-    }
-    const cx<T> *own = tile + (size_t)lr * SW;
-    cx<T> o[SW];
-#pragma unroll
-    for (int c = 0; c < SW; ++c) {
-      o[c].re = fma(diag, own[c].re, acc[c].re);
-      o[c].im = fma(diag, own[c].im, acc[c].im);
-    }
-    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)b * r + c0);
-    float w[2 * SW];
-#pragma unroll
-    for (int c = 0; c < SW; ++c) { w[2 * c] = (float)0; w[2 * c + 1] = (float)0; }
-    if (sizeof(T) == 4) {
-#pragma unroll
-      for (int c = 0; c < SW; ++c) { w[2 * c] = (float)o[c].re; w[2 * c + 1] = (float)o[c].im; }
-      dst[0] = make_float4(w[0], w[1], w[2], w[3]);
-      dst[1] = make_float4(w[4], w[5], w[6], w[7]);
-    } else {
-      double2 *dd = reinterpret_cast<double2 *>(dst);
-      dd[0] = make_double2((double)o[0].re, (double)o[0].im);
-      dd[1] = make_double2((double)o[SW - 1].re, (double)o[SW - 1].im);
-    }
-  }
-}
-
-// ------------------------------------------------ H.V, slab-major, swizzled shared tiles
-// Same traversal as hv2_kernel (slab by slab, so the slab being processed stays resident in L2
-// and partner rows outside the tile are L2 hits).  The tile is held as 16-byte chunks; the two
-// halves of a row swap places in every other group of four rows, so the 8 lanes of a
-// quarter-warp reading 8 aligned rows (or any XOR image of them, which is what a bit-flip
-// partner lookup reads) touch 8 distinct bank groups with 128-bit loads.  Bonds are taken BATCH
-// at a time: their partner loads (shared or global) are issued before the multiply-adds, so up
-// to BATCH L2 round trips per row are in flight together.
-// A 32-byte slab row as two 16-byte chunks, read as real words of type T.
-struct Row32 {
-  float4 v[2];
-};
-template <typename T> __device__ __forceinline__ T row_word(const Row32 &x, int q);
-template <> __device__ __forceinline__ float row_word<float>(const Row32 &x, int q) {
-  const float4 &c = x.v[q >> 2];
-  const int i = q & 3;
-  return i == 0 ? c.x : (i == 1 ? c.y : (i == 2 ? c.z : c.w));
-}
-template <> __device__ __forceinline__ double row_word<double>(const Row32 &x, int q) {
-  const float4 &c = x.v[q >> 1];
-  return (q & 1) ? __hiloint2double(__float_as_int(c.w), __float_as_int(c.z))
-                 : __hiloint2double(__float_as_int(c.y), __float_as_int(c.x));
-}
-template <typename T> __device__ __forceinline__ void row_set(Row32 &x, const T (&w)[32 / sizeof(T)]);
-template <> __device__ __forceinline__ void row_set<float>(Row32 &x, const float (&w)[8]) {
-  x.v[0] = make_float4(w[0], w[1], w[2], w[3]);
-  x.v[1] = make_float4(w[4], w[5], w[6], w[7]);
-}
-template <> __device__ __forceinline__ void row_set<double>(Row32 &x, const double (&w)[4]) {
-  x.v[0] = make_float4(__int_as_float(__double2loint(w[0])), __int_as_float(__double2hiint(w[0])),
-                       __int_as_float(__double2loint(w[1])), __int_as_float(__double2hiint(w[1])));
-  x.v[1] = make_float4(__int_as_float(__double2loint(w[2])), __int_as_float(__double2hiint(w[2])),
-                       __int_as_float(__double2loint(w[3])), __int_as_float(__double2hiint(w[3])));
-}
-
-template <typename T, int BATCH>
-__global__ void __launch_bounds__(256) hv3_kernel(const __grid_constant__ ModelArgs M, const cx<T> *__restrict__ X,
-                                                  cx<T> *__restrict__ Y, long long N, int r, int tbits) {
-  constexpr int SW = 32 / sizeof(cx<T>);   // complex elements per slab row
-  constexpr int NW = 32 / sizeof(T);       // real words per slab row
-  extern __shared__ __align__(16) float4 hv3_tile[];
-  const uint32_t TR = 1u << tbits;
-  const long long ntile = N >> tbits;
-  const int slab = (int)(blockIdx.x / ntile);
-  const uint32_t t0 = (uint32_t)((blockIdx.x % ntile) << tbits);
-  const int c0 = slab * SW;
-  for (uint32_t e = threadIdx.x; e < 2 * TR; e += blockDim.x) {
-    const uint32_t lr = e >> 1, h = e & 1u;
-    hv3_tile[2 * lr + (h ^ ((lr >> 2) & 1u))] =
-        __ldg(reinterpret_cast<const float4 *>(X + (size_t)(t0 + lr) * r + c0) + h);
-  }
-  __syncthreads();
-  for (uint32_t lr = threadIdx.x; lr < TR; lr += blockDim.x) {
-    const uint32_t b = t0 + lr;
-    T diag = (T)(M.c0 + M.bz * (0.5 * M.n - (double)__popc(b)));
-    T acc[NW];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) acc[q] = (T)0;
-    for (int k0 = 0; k0 < M.nb; k0 += BATCH) {
-      Row32 p[BATCH];
-      T jj[BATCH];
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u) {
-        const int k = k0 + u;
-        jj[u] = (T)0;
-        p[u].v[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        p[u].v[1] = p[u].v[0];
-        if (k < M.nb && (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u)) {
-          diag -= (T)M.jz[k];
-          jj[u] = (T)M.jxy[k];
-          const uint32_t mk = M.mask[k];
-          if (mk < TR) {
-            const uint32_t pr = lr ^ mk, s = (pr >> 2) & 1u;
-            p[u].v[0] = hv3_tile[2 * pr + s];
-            p[u].v[1] = hv3_tile[2 * pr + (s ^ 1u)];
-          } else {
-            const float4 *g = reinterpret_cast<const float4 *>(X + (size_t)(b ^ mk) * r + c0);
-            p[u].v[0] = __ldg(g);
-            p[u].v[1] = __ldg(g + 1);
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < BATCH; ++u)
-#pragma unroll
-        for (int q = 0; q < NW; ++q) acc[q] = fma(jj[u], row_word<T>(p[u], q), acc[q]);
-    }
-    Row32 own, o;
-    {
-      const uint32_t s = (lr >> 2) & 1u;
-      own.v[0] = hv3_tile[2 * lr + s];
-      own.v[1] = hv3_tile[2 * lr + (s ^ 1u)];
-    }
-    T ow[NW];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) ow[q] = fma(diag, row_word<T>(own, q), acc[q]);
-    row_set<T>(o, ow);
-    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)b * r + c0);
-    dst[0] = o.v[0];
-    dst[1] = o.v[1];
-  }
-}
-
-// ------------------------------------------------ H.V, slab tiles staged by TMA
-// Same tiles and bond handling as hv3_kernel, but no thread loads global memory: the tile of
-// 2^tbits rows of the CTA's 32-byte column slab and every partner tile a bond reaches outside
-// it (the tile t0 ^ (mask & ~(TR - 1)), rows permuted by the mask's low bits) are copied into
-// shared memory by the tensor-memory accelerator (2-D boxes of 256 rows x 32 bytes), so the
-// gathers run as bulk copies instead of per-lane 32-byte requests.  Partner tiles stream
-// through two buffers: while the threads add one, the next is in flight.  A bond whose two
-// bits both lie above the tile is active for all rows of the tile or for none, so only active
-// ones are fetched.  CTAs go tile by tile (all slabs of a tile, then the next tile), so whole
-// 128-byte lines of the block are in use together.  Every wait on a copy is bounded; a wait
-// that runs out sets ST_TIMEOUT and the kernel finishes without using that buffer.
-__device__ __forceinline__ uint32_t hv5_smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool hv5_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    uint32_t done;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    if (done) return true;
-    if (it > 32) __nanosleep(64);
-  }
-  return false;
-}
-
-// Row lr of a dense [TR][32 B] buffer; the two 16-byte halves are read in an order that
-// depends on bit 2 of the row, so a quarter-warp reading 8 rows of an aligned group (or an XOR
-// image of one) touches 8 distinct bank groups.
-__device__ __forceinline__ Row32 hv5_row(const float4 *buf, uint32_t lr) {
-  const uint32_t s = (lr >> 2) & 1u;
-  const float4 a = buf[2 * lr + s], b = buf[2 * lr + (s ^ 1u)];
-  Row32 o;
-  o.v[0] = s ? b : a;
-  o.v[1] = s ? a : b;
-  return o;
-}
-
-template <typename T, int TB, int NBUF>
-__global__ void __launch_bounds__(256) hv5_kernel(const __grid_constant__ CUtensorMap tmx,
-                                                  const __grid_constant__ ModelArgs M, cx<T> *__restrict__ Y,
-                                                  long long N, int r, int tbits, int *status) {
-  constexpr int NW = 32 / sizeof(T);
-  constexpr int RPT = (1 << TB) / 256;        // rows per thread
-  extern __shared__ __align__(1024) float4 hv5_buf[];   // [1 + NBUF][TR][2]
-  __shared__ __align__(8) unsigned long long bar[1 + NBUF];
-  __shared__ int ext_k[MAX_BONDS];
-  __shared__ int n_ext;
-  const uint32_t TR = 1u << TB;
-  (void)tbits;
-  const long long ntile = N >> TB;
-  const int nslab = (int)(gridDim.x / ntile);
-  const int slab = (int)(blockIdx.x % nslab);
-  const uint32_t t0 = (uint32_t)((blockIdx.x / nslab) << TB);
-  const int x0 = slab * 8;                    // first 4-byte word of the slab in a row
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    int n = 0;
-    for (int k = 0; k < M.nb; ++k) {
-      const uint32_t hi = M.mask[k] & ~(TR - 1), lo = M.mask[k] & (TR - 1);
-      if (!hi) continue;
-      if (!lo && !(((t0 >> M.bi[k]) ^ (t0 >> M.bj[k])) & 1u)) continue;   // inactive on this tile
-      ext_k[n++] = k;
-    }
-    n_ext = n;
-    for (int i = 0; i < 1 + NBUF; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hv5_smem_addr(&bar[i])));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  __syncthreads();
-  const int ne = n_ext;
-  auto issue = [&](int b, uint32_t row0) {   // one thread
-    const uint32_t ba = hv5_smem_addr(&bar[b]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ba), "r"(TR * 32u) : "memory");
-    for (uint32_t y = 0; y < TR; y += 256) {
-      const uint32_t dst = hv5_smem_addr(hv5_buf + (size_t)b * TR * 2 + (size_t)y * 2);
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::
-              "r"(dst), "l"(reinterpret_cast<uint64_t>(&tmx)), "r"(x0), "r"((int)(row0 + y)), "r"(ba)
-          : "memory");
-    }
-  };
-  if (tid == 0) {
-    issue(0, t0);
-    for (int e = 0; e < NBUF && e < ne; ++e) issue(1 + e, t0 ^ (M.mask[ext_k[e]] & ~(TR - 1)));
-  }
-  bool ok = hv5_wait(hv5_smem_addr(&bar[0]), 0);
-  const float4 *own = hv5_buf;
-  T acc[RPT][NW], diag[RPT];
-#pragma unroll
-  for (int i = 0; i < RPT; ++i) {
-    const uint32_t lr = tid + 256u * i, b = t0 + lr;
-    diag[i] = (T)(M.c0 + M.bz * (0.5 * M.n - (double)__popc(b)));
-#pragma unroll
-    for (int q = 0; q < NW; ++q) acc[i][q] = (T)0;
-    for (int k = 0; k < M.nb; ++k) {
-      if (((b >> M.bi[k]) ^ (b >> M.bj[k])) & 1u) {
-        diag[i] -= (T)M.jz[k];
-        if (M.mask[k] < TR) {
-          const T j = (T)M.jxy[k];
-          const Row32 p = hv5_row(own, lr ^ M.mask[k]);
-#pragma unroll
-          for (int q = 0; q < NW; ++q) acc[i][q] = fma(j, row_word<T>(p, q), acc[i][q]);
-        }
-      }
-    }
-  }
-  for (int e = 0; e < ne; ++e) {
-    const int b = 1 + (e % NBUF);
-    const bool got = hv5_wait(hv5_smem_addr(&bar[b]), (uint32_t)((e / NBUF) & 1));
-    ok = ok && got;
-    const int k = ext_k[e];
-    const uint32_t lo = M.mask[k] & (TR - 1);
-    const T j = (T)M.jxy[k];
-    const float4 *pb = hv5_buf + (size_t)b * TR * 2;
-    if (got) {
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const uint32_t lr = tid + 256u * i, bb = t0 + lr;
-        if (((bb >> M.bi[k]) ^ (bb >> M.bj[k])) & 1u) {
-          const Row32 p = hv5_row(pb, lr ^ lo);
-#pragma unroll
-          for (int q = 0; q < NW; ++q) acc[i][q] = fma(j, row_word<T>(p, q), acc[i][q]);
-        }
-      }
-    }
-    __syncthreads();   // every thread is done with buffer b
-    if (tid == 0 && e + NBUF < ne) {
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      issue(b, t0 ^ (M.mask[ext_k[e + NBUF]] & ~(TR - 1)));
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < RPT; ++i) {
-    const uint32_t lr = tid + 256u * i, b = t0 + lr;
-    const Row32 o0 = hv5_row(own, lr);
-    T ow[NW];
-#pragma unroll
-    for (int q = 0; q < NW; ++q) ow[q] = fma(diag[i], row_word<T>(o0, q), acc[i][q]);
-    Row32 o;
-    row_set<T>(o, ow);
-    float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)b * r + slab * (32 / sizeof(cx<T>)));
-    dst[0] = o.v[0];
-    dst[1] = o.v[1];
-  }
-  if (!ok && tid == 0 && status) atomicOr(status, ST_TIMEOUT);
-}
-
 // ------------------------------------------------------ accumulation
 // Error-free sum: s + e == a + b exactly (Knuth TwoSum).
 __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float b) {
@@ -490,11 +158,6 @@ template <> struct Acc<float> {
 
 // ------------------------------------------------------ fused tile pass
 constexpr int TS_THREADS = 256;
-static bool g_force_v1 = false;   // selects the unblocked kernel (A/B comparison)
-static bool g_hv_v2 = false;       // selects the unswizzled slab-major H.V kernel (A/B comparison)
-static bool g_hv_v3 = false;       // selects the slab kernel with per-lane partner loads (A/B comparison)
-static PFN_cuTensorMapEncodeTiled_v12000 g_tmap_encode = nullptr;   // driver entry point (TMA descriptors)
-static int g_hv5_cfg = 0;          // tile rows of the TMA H.V kernel: 0 = 256, 1 = 512, 2 = 1024 (A/B)
 
 
 template <typename T>
@@ -842,9 +505,9 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
 // into compensated FP32 pairs (TwoSum) in shared memory.  Lane = phase * TPW + micro-tile, so
 // the G loads of a quarter-warp are one row (distinct 16-byte columns) and the block loads of
 // a half-warp are two rows of two columns: no bank conflicts at r = 16.
-template <int R, int TR, int GMAX>
-__global__ void __launch_bounds__(256, (TR <= 32 ? 2 : 1)) ts3_kernel(const __grid_constant__ TSArgs a,
-                                                                     const cx<float> *__restrict__ coefg) {
+template <int R, int TR, int GMAX, int MINB = (TR <= 32 ? 2 : 1)>
+__global__ void __launch_bounds__(256, MINB) ts3_kernel(const __grid_constant__ TSArgs a,
+                                                       const cx<float> *__restrict__ coefg) {
   constexpr int RS = R + 2;
   constexpr int MTS = R * R / 4;
   constexpr int NPH = 256 / MTS;
@@ -1246,75 +909,10 @@ void launch_reduce(const double *partial, int nparts, int len_doubles, double *o
   reduce_kernel<<<(len_doubles + 255) / 256, 256, 0, st>>>(tmp, nslice, len_doubles, out);
 }
 
-// Tensor map of an N x r block viewed as N rows of (2 or 4) r 4-byte words, box 256 rows x 8 words.
-static bool hv5_tensor_map(CUtensorMap *tm, bool fp64, const void *X, long long N, int r) {
-  if (!g_tmap_encode) return false;
-  const cuuint64_t words = (cuuint64_t)r * (fp64 ? 4 : 2);
-  const cuuint64_t dims[2] = {words, (cuuint64_t)N};
-  const cuuint64_t strides[1] = {words * 4};
-  const cuuint32_t box[2] = {8, 256};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult rc = g_tmap_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(X), dims, strides, box, estr,
-                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return rc == CUDA_SUCCESS;
-}
-
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                int *status) {
-  const size_t rowb = (size_t)r * (fp64 ? 16 : 8);
   if (launch_hv6(fp64, M, X, Y, N, r, nsm, st, status)) return;
-  if (M.cplx) {   // complex amplitudes or one-bit partners: the generic per-row gather
-    auto grid_c = [&](int cpt) {
-      long long g = (N * (r / cpt) + 255) / 256, cap = (long long)nsm * 16;
-      return (int)(g < cap ? g : cap);
-    };
-    ::lrei::count_launch();
-    if (fp64) hv_kernel<double, 1><<<grid_c(1), 256, 0, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r);
-    else hv_kernel<float, 1><<<grid_c(1), 256, 0, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r);
-    return;
-  }
-  // TMA-staged tiles of 32-byte row slabs: the CTA's own tile and two partner-tile buffers
-  if (!g_hv_v2 && !g_hv_v3 && !g_force_v1 && M.n >= 10 && rowb % 32 == 0 &&
-      (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
-    CUtensorMap tm;
-    if (hv5_tensor_map(&tm, fp64, X, N, r)) {
-      auto go = [&](auto kd, auto kf, int tb, int nbuf) {
-        const long long ntile = N >> tb;
-        const int grid = (int)(ntile * (long long)(rowb / 32));
-        const size_t bytes = (size_t)(1 + nbuf) * ((size_t)1 << tb) * 32;
-        ::lrei::count_launch();
-        if (fp64) kd<<<grid, 256, bytes, st>>>(tm, M, (cx<double> *)Y, N, r, tb, status);
-        else kf<<<grid, 256, bytes, st>>>(tm, M, (cx<float> *)Y, N, r, tb, status);
-      };
-      // 256-row tiles, two partner buffers (24 KB per CTA, up to 8 CTAs per SM): 0.231 ms at n=20,
-      // r=16; 512-row tiles 0.244 ms, 1024-row tiles 0.280 ms, four buffers no better
-      switch (g_hv5_cfg) {
-        case 1: go(hv5_kernel<double, 9, 2>, hv5_kernel<float, 9, 2>, 9, 2); break;
-        case 2: go(hv5_kernel<double, 10, 2>, hv5_kernel<float, 10, 2>, 10, 2); break;
-        default: go(hv5_kernel<double, 8, 2>, hv5_kernel<float, 8, 2>, 8, 2); break;
-      }
-      return;
-    }
-  }
-  const int sw = fp64 ? 2 : 4;
-  if (r % sw == 0 && !g_force_v1) {
-    int tbits = M.n < 11 ? M.n : 11;
-    const long long TR = 1LL << tbits;
-    const long long ntile = (N + TR - 1) / TR;
-    const int grid = (int)(ntile * (r / sw));
-    const size_t bytes = (size_t)TR * 32;
-    ::lrei::count_launch();
-    if (g_hv_v2) {
-      if (fp64) hv2_kernel<double><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
-      else hv2_kernel<float><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
-    } else {
-      // four bonds per batch: eight measured 10% slower (register pressure)
-      if (fp64) hv3_kernel<double, 4><<<grid, 256, bytes, st>>>(M, (const cx<double> *)X, (cx<double> *)Y, N, r, tbits);
-      else hv3_kernel<float, 4><<<grid, 256, bytes, st>>>(M, (const cx<float> *)X, (cx<float> *)Y, N, r, tbits);
-    }
-    return;
-  }
+  // rows that are not a multiple of 16 bytes, or fewer than 16 rows: the per-row gather
   auto grid_for = [&](int cpt) {
     long long total = N * (r / cpt);
     long long g = (total + 255) / 256;
@@ -1483,17 +1081,6 @@ void launch_check_finite(bool fp64, const void *X, long long N, int r, int *stat
 namespace lrei {
 // Raise the dynamic shared-memory limit of every tile kernel once (outside any stream capture).
 int ts_init() {
-  g_hv_v2 = getenv("LREI_HV2") != nullptr;
-  g_hv_v3 = getenv("LREI_HV3") != nullptr;
-  if (const char *e = getenv("LREI_HV5_CFG")) g_hv5_cfg = atoi(e);
-  {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      g_tmap_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    cudaGetLastError();
-  }
   if (hv6_init()) return -1;
   const int lim = 210 * 1024;
   cudaError_t e = cudaSuccess;
@@ -1527,16 +1114,6 @@ int ts_init() {
   set((const void *)ts2_kernel<float, 4, 2>);
   set((const void *)ts2_kernel<float, 2, 2>);
   set((const void *)ts2_kernel<float, 1, 2>);
-  set((const void *)hv2_kernel<double>);
-  set((const void *)hv2_kernel<float>);
-  set((const void *)hv5_kernel<double, 10, 2>);
-  set((const void *)hv5_kernel<float, 10, 2>);
-  set((const void *)hv5_kernel<double, 9, 2>);
-  set((const void *)hv5_kernel<float, 9, 2>);
-  set((const void *)hv5_kernel<double, 8, 2>);
-  set((const void *)hv5_kernel<float, 8, 2>);
-  set((const void *)hv3_kernel<double, 4>);
-  set((const void *)hv3_kernel<float, 4>);
   set((const void *)obs_kernel<double>);
   set((const void *)obs_kernel<float>);
   return e == cudaSuccess ? 0 : -1;

@@ -106,7 +106,7 @@ def test_trained_network_gain_over_plain_rule():
     net, loss = ctl.fit(X, Y, iters=2000, lr=2e-3)
     assert loss < 0.5 * float(np.var(Y)) + 1e-6      # better than the mean (loss = half the mean square)
     w = li.workload(4, 9, n=9, r=4, kappa=0.1)
-    t_end, tol = 1.0, 1e-7
+    t_end, tol = 1.0, 1e-8
     ref = _reference(w, t_end, h=0.005)
     o_p, st_p = _run(w, t_end, tol, 0, judge_every=8)
     o_l, st_l = _run(w, t_end, tol, 1, judge_every=8, net=net)
