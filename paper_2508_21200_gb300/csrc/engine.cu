@@ -783,7 +783,9 @@ int dalloc(lrei_ctx *c, void **p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess) return LREI_ERR_OOM;
   c->allocs.push_back(*p);
-  cudaMemset(*p, 0, bytes ? bytes : 16);
+  // zeroed on the context's stream, so the zeros land before any later work of the context
+  // (a memset on the legacy stream is not ordered with a non-blocking stream)
+  if (cudaMemsetAsync(*p, 0, bytes ? bytes : 16, c->st) != cudaSuccess) return LREI_ERR_CUDA;
   return LREI_OK;
 }
 template <typename P>
@@ -1674,7 +1676,9 @@ int lrei_set_state(lrei_ctx *c, const void *V_dev, int r, int ld, int dtype, con
     if (c->lam0[i] < -1e-12) return LREI_ERR_TRACE;
     if (c->lam0[i] < 0.0) c->lam0[i] = 0.0;
   }
-  cudaMemcpy(c->lam0_dev, c->lam0.data(), r * sizeof(double), cudaMemcpyHostToDevice);
+  // on the context's stream: a plain copy from pageable memory may return before the data lands
+  LREI_CUDA_TRY(cudaMemcpyAsync(c->lam0_dev, c->lam0.data(), r * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  LREI_CUDA_TRY(cudaStreamSynchronize(c->st));
   c->t = 0.0;
   c->has_state = true;
   return LREI_OK;
@@ -2323,9 +2327,10 @@ int batch_run(lrei_batch *b, double dt, int nsteps) {
   }
   if (dt != b->dt) {
     for (lrei_ctx *c : b->ctx) {
-      LREI_CUDA_TRY(cudaMemcpy(c->dt_dev, &dt, sizeof(double), cudaMemcpyHostToDevice));
+      LREI_CUDA_TRY(cudaMemcpyAsync(c->dt_dev, &dt, sizeof(double), cudaMemcpyHostToDevice, b->st));
       c->dt_cur = dt;
     }
+    LREI_CUDA_TRY(cudaStreamSynchronize(b->st));
     b->dt = dt;
   }
   for (int i = 0; i < nsteps; ++i) LREI_CUDA_TRY(cudaGraphLaunch(b->exec, b->st));

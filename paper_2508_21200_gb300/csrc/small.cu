@@ -645,13 +645,22 @@ void sm_scale_cols(zd *A, int lda, int M, int N, double s, cudaStream_t st) {
   ::lrei::count_launch(); scale_kernel<<<grid_for((long long)M * N), 256, 0, st>>>(A, lda, M, N, s);
 }
 
+// Columns k..k+r-1 of the Hermitian Gram G from the measured block R ((k + r) x r) and their
+// mirror rows.  Inside the new r x r diagonal block only R's upper triangle is used (the lower one
+// is its conjugate), so every entry of G has exactly one writer: R's two triangles differ in the
+// last bit, and two threads storing both into one entry would make the result depend on which
+// store lands last.
 __global__ void store_gram_cols_kernel(const zd *R, int ldr, int k, int r, zd *G, int ldg) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (k + r) * r; e += gridDim.x * blockDim.x) {
     const int i = e % (k + r), j = e / (k + r);
+    if (i > k + j) continue;   // below the diagonal of the new block: written as the mirror of (k + j, i)
     const zd v = R[(size_t)j * ldr + i];
-    G[(size_t)(k + j) * ldg + i] = v;
-    G[(size_t)i * ldg + (k + j)] = conj(v);
-    if (i == k + j) G[(size_t)(k + j) * ldg + i] = mk<double>(v.re, 0);
+    if (i == k + j) {
+      G[(size_t)(k + j) * ldg + i] = mk<double>(v.re, 0);
+    } else {
+      G[(size_t)(k + j) * ldg + i] = v;
+      G[(size_t)i * ldg + (k + j)] = conj(v);
+    }
   }
 }
 void sm_store_gram_cols(const zd *R, int ldr, int k, int r, zd *G, int ldg, cudaStream_t st) {
