@@ -452,12 +452,12 @@ def run_ours(args):
     alg_bytes = 2 * N * r * 8
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / hv_s / 1e9
-    roof_hv = {"kernel": "hv6_kernel<float,2> (Y = H V, matrix-free, full 128-byte rows, N=2^20, r=16)", "bound": "hbm",
+    roof_hv = {"kernel": "hv7_kernel<float,2,8,0,3> (Y = H V, matrix-free, 32 KB tiles, partner tiles by bulk copy, N=2^20, r=16)", "bound": "hbm",
                "achieved": round(achieved, 1), "peak": peak,
                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6800",
                "unit": "GB/s", "frac": round(achieved / peak, 4), "ms_per_launch": round(hv_s * 1e3, 4),
                "algorithmic_bytes_per_launch": alg_bytes,
-               "traffic": _traffic_from_profile("paper_2508_21200_gb300/csrc/tsk.cu", "hv_c64_n20_r16")}
+               "traffic": _traffic_from_profile("paper_2508_21200_gb300/csrc/hv.cu", "hv_c64_n20_r16")}
     del Vb, Yb
 
     # ---- end to end through the public API: pinned host V -> device, step, observables -> host

@@ -8,25 +8,21 @@
 // row (two complex64 or one complex128) is updated independently.
 //
 // Work decomposition.  A CTA owns tiles of TR = 2^tb consecutive rows (about 32 KB), one tile
-// at a time, and its threads own 16-byte words of rows (ch = row bytes / 16 threads per row,
-// each thread the same word of RPT rows of the tile).
-// Bonds fall into three classes relative to the tile bits:
-//  * in-tile (both bits below tb): the partner row is in the same tile.  The tile is copied
-//    into shared memory by the tensor-memory accelerator (bulk copy, mbarrier completion), and
-//    which in-tile bonds are active on row lr depends only on lr, so a per-CTA table holds the
-//    active set (a bitmask) and its diagonal contribution for every lr;
+// at a time; thread (slot, c) of its 8 consumer warps owns 16-byte word c of rows slot + i rp
+// (ch = row bytes / 16 words per row, rp = 256 / ch rows per pass).  Terms fall into three
+// classes relative to the tile bits:
+//  * in-tile (both bits below tb): the partner row is in the same tile; which in-tile terms
+//    are active on row lr depends only on lr, so a per-CTA table holds the active set (a
+//    bitmask) and its diagonal share for every lr;
 //  * outside (both bits at or above tb): active for every row of a tile or for none, with the
-//    partner rows forming the tile t0 ^ m.  Per tile, the active ones and their diagonal
-//    contribution are listed once; the thread then goes bond by bond, loading the partner words
-//    of all its RPT rows as one group of independent 16-byte loads (read-only path, not
-//    allocated in L1) before adding them, two bonds per iteration, so up to 2 RPT L2 requests
-//    are in flight per thread;
-//  * straddling (one bit on each side): activity per row from one low bit and one tile bit;
-//    the partner row is loaded from global memory like an outside bond's.
-// The own tile is single- or double-buffered (a template parameter; the library runs several
-// single-buffered CTAs per SM, which overlap each other's copies).  Every wait on a copy is bounded; a wait that runs out sets ST_TIMEOUT, the tile
-// is skipped, and before the kernel exits thread 0 waits (again bounded) for every copy it
-// issued, so no copy is left in flight into released shared memory.
+//    partner rows forming the whole tile t0 ^ m;
+//  * straddling (one bit on each side): active on the rows whose low bit differs from the
+//    tile's high bit; their partners fill half of tile t0 ^ m (a contiguous half when the low
+//    bit is the top row bit).
+// The own tile and every partner tile needed by the tile are brought into shared memory by
+// bulk copies (hv7_kernel below), so the bytes in flight are bounded by shared memory rather
+// than by registers.  Every wait on a copy is bounded; see the kernel's comment for the error
+// path.
 #include "common.cuh"
 
 #include <cstring>
@@ -103,38 +99,46 @@ struct HvPlan {
   double a0r[HV_MAX_TERMS], a0i[HV_MAX_TERMS], a1r[HV_MAX_TERMS], a1i[HV_MAX_TERMS];
 };
 
-// RPT: rows per thread and tile (tile bytes / 16 / 256 threads; 8 for the 32 KB tiles of the
-// launcher).  CPLX: complex amplitudes or one-bit terms present.  ROWMAJOR: each thread takes its
-// rows one at a time and issues the outside partner loads of a row LIF at a time; otherwise it
-// goes term by term over all its rows (RPT loads per term).  MINB: CTAs per SM to fit.
-template <typename T, int NBUF, int RPT, bool CPLX, bool ROWMAJOR, int LIF, int MINB>
-__global__ void __launch_bounds__(256, MINB) hv6_kernel(const __grid_constant__ HvPlan P,
+// ------------------------------------------------------- hv7: partner tiles by bulk copy
+// The rows of an outside term's partners form one whole tile (t0 ^ m), and those of a straddling
+// bond half of one (the rows whose low bit equals the tile's high bit).  hv7 brings every partner
+// tile into shared memory with bulk copies instead of per-thread loads, so the bytes in flight
+// are bounded by shared memory rather than by registers: a ring of NB tile buffers, filled by one
+// producer warp (one elected lane issues the copies; a full barrier per buffer counts the bytes)
+// and drained by 8 consumer warps (an empty barrier per buffer counts the warps that are done).
+// Per tile the chunks are the own tile, then each straddling bond's half or whole partner tile,
+// then each outside term active on the tile; the consumers keep the tile's output words in
+// registers across its chunks and store them once.  Every wait is bounded: a consumer or the
+// producer that gives up sets ST_TIMEOUT and a shared abort flag that ends everyone's loop, and
+// the producer waits (bounded) for each buffer's last copy before the CTA exits.
+template <typename T, int NB, int RPT, bool CPLX, int MINB, int SUSP = 0>
+__global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ HvPlan P,
                                                   const typename W16<T>::V *__restrict__ X,
                                                   typename W16<T>::V *__restrict__ Y, int *status) {
   using V = typename W16<T>::V;
-  extern __shared__ __align__(128) unsigned char hv6_smem[];
+  extern __shared__ __align__(128) unsigned char hv7_smem[];
   const int tb = P.tb, ch = P.ch;
   const uint32_t TR = 1u << tb;
-  V *buf = reinterpret_cast<V *>(hv6_smem);                                           // [NBUF][TR][ch]
-  unsigned long long *rmask = reinterpret_cast<unsigned long long *>(buf + (size_t)NBUF * TR * ch);   // [TR]
-  T *rdiag = reinterpret_cast<T *>(rmask + TR);                                        // [TR]
-  __shared__ __align__(8) unsigned long long bar[NBUF];
-  __shared__ uint32_t imask[64], smask[HV_MAX_TERMS], fmask[HV_MAX_TERMS];
-  __shared__ T i0r[64], i0i[64], i1r[64], i1i[64];                    // in-tile amplitudes
-  __shared__ T s0r[HV_MAX_TERMS], s0i[HV_MAX_TERMS], s1r[HV_MAX_TERMS], s1i[HV_MAX_TERMS], sjz[HV_MAX_TERMS];
-  __shared__ T fr[HV_MAX_TERMS], fi[HV_MAX_TERMS];                    // outside amplitudes on this tile
-  __shared__ uint8_t isb[64], slo[HV_MAX_TERMS], ssb[HV_MAX_TERMS], sselin[HV_MAX_TERMS];
-  __shared__ unsigned long long sflip, ssel;
-  __shared__ T dconst;
-  __shared__ int nfa;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int rp = nt / ch;                    // rows per pass
-  const int slot = tid / ch, c = tid - slot * ch;
+  V *buf = reinterpret_cast<V *>(hv7_smem);                                                   // [NB][TR][ch]
+  unsigned long long *rmask = reinterpret_cast<unsigned long long *>(buf + (size_t)NB * TR * ch);   // [TR]
+  T *rdiag = reinterpret_cast<T *>(rmask + TR);                                                // [TR]
+  __shared__ __align__(8) unsigned long long full[NB], empty[NB];
+  __shared__ volatile int abort_flag;
+  __shared__ uint32_t imask[64];
+  __shared__ T i0r[64], i0i[64], i1r[64], i1i[64];
+  __shared__ uint8_t isb[64];
+  __shared__ uint32_t shi[HV_MAX_TERMS];   // straddling: partner tile offset (mask >> tb)
+  __shared__ uint8_t slo[HV_MAX_TERMS], shb[HV_MAX_TERMS], ssb[HV_MAX_TERMS], ssel_in[HV_MAX_TERMS];
+  __shared__ T sjz[HV_MAX_TERMS], s0r[HV_MAX_TERMS], s0i[HV_MAX_TERMS], s1r[HV_MAX_TERMS], s1i[HV_MAX_TERMS];
+  __shared__ uint32_t fhi[HV_MAX_TERMS];   // outside: partner tile offset (mask >> tb)
+  __shared__ uint8_t fbi[HV_MAX_TERMS], fbj[HV_MAX_TERMS], ftwo[HV_MAX_TERMS], fsb[HV_MAX_TERMS];
+  __shared__ T f0r[HV_MAX_TERMS], f0i[HV_MAX_TERMS], f1r[HV_MAX_TERMS], f1i[HV_MAX_TERMS];
+  const int tid = threadIdx.x;
   const long long ntiles = P.N >> tb;
   const int nI = P.nI, nS = P.nS, nF = P.nF;
+  const uint32_t TB = TR * (uint32_t)ch * 16u;   // tile bytes
 
-  // per-CTA tables: in-tile terms' active set and diagonal share for every row of a tile
-  for (uint32_t lr = tid; lr < TR; lr += nt) {
+  for (uint32_t lr = tid; lr < TR; lr += blockDim.x) {
     unsigned long long m = 0;
     double d = -P.bz * (double)__popc(lr);
     for (int k = 0; k < nI; ++k)
@@ -145,278 +149,303 @@ __global__ void __launch_bounds__(256, MINB) hv6_kernel(const __grid_constant__ 
     rmask[lr] = m;
     rdiag[lr] = (T)d;
   }
-  for (int k = tid; k < nI; k += nt) {
+  for (int k = tid; k < nI; k += blockDim.x) {
     imask[k] = P.mask[k];
     i0r[k] = (T)P.a0r[k]; i0i[k] = (T)P.a0i[k]; i1r[k] = (T)P.a1r[k]; i1i[k] = (T)P.a1i[k];
     isb[k] = P.sb[k];
   }
-  for (int k = tid; k < nS; k += nt) {
+  for (int k = tid; k < nS; k += blockDim.x) {
     const int q = nI + k;
-    smask[k] = P.mask[q];
-    s0r[k] = (T)P.a0r[q]; s0i[k] = (T)P.a0i[q]; s1r[k] = (T)P.a1r[q]; s1i[k] = (T)P.a1i[q];
-    sjz[k] = (T)P.jz[q];
+    shi[k] = P.mask[q] >> tb;
     slo[k] = P.bi[q];
+    shb[k] = P.bj[q];
     ssb[k] = P.sb[q];
-    sselin[k] = P.sb[q] < tb ? 1 : 0;   // selector inside the tile (from the row) or a tile bit
+    ssel_in[k] = P.sb[q] < tb ? 1 : 0;
+    sjz[k] = (T)P.jz[q];
+    s0r[k] = (T)P.a0r[q]; s0i[k] = (T)P.a0i[q]; s1r[k] = (T)P.a1r[q]; s1i[k] = (T)P.a1i[q];
+  }
+  for (int k = tid; k < nF; k += blockDim.x) {
+    const int q = nI + nS + k;
+    fhi[k] = P.mask[q] >> tb;
+    fbi[k] = P.bi[q];
+    fbj[k] = P.bj[q];
+    ftwo[k] = P.two[q];
+    fsb[k] = P.sb[q];
+    f0r[k] = (T)P.a0r[q]; f0i[k] = (T)P.a0i[q]; f1r[k] = (T)P.a1r[q]; f1i[k] = (T)P.a1i[q];
   }
   if (tid == 0) {
-    for (int i = 0; i < NBUF; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bar[i])));
+    abort_flag = 0;
+    for (int i = 0; i < NB; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(smem_u32(&empty[i])));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
 
-  const uint32_t tile_bytes = TR * (uint32_t)ch * 16u;
-  auto issue = [&](int b, long long tile) {   // thread 0 only
-    const uint32_t ba = smem_u32(&bar[b]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(ba), "r"(tile_bytes) : "memory");
-    const char *src = reinterpret_cast<const char *>(X) + (size_t)tile * tile_bytes;
-    const uint32_t dst = smem_u32(buf + (size_t)b * TR * ch);
-    for (uint32_t off = 0; off < tile_bytes; off += 16384u) {
-      const uint32_t sz = (tile_bytes - off) < 16384u ? (tile_bytes - off) : 16384u;
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst + off),
-                   "l"(src + off), "r"(sz), "r"(ba)
-                   : "memory");
+  // a straddling bond copies the half of its partner tile that holds the partners (rows whose
+  // bit slo equals the tile's bit) when slo is the top row bit, else the whole tile
+  auto half_of = [&](int s) { return (int)slo[s] == tb - 1; };
+  auto outside_active = [&](int f, uint32_t t0) {
+    return !ftwo[f] || (((t0 >> fbi[f]) ^ (t0 >> fbj[f])) & 1u);
+  };
+  // bounded wait that also gives up once another warp has aborted
+  auto wait_bar = [&](unsigned long long *bar, uint32_t parity) -> bool {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < (SUSP ? (1 << 16) : (1 << 22)); ++it) {
+      uint32_t done;
+      if constexpr (SUSP > 0) {
+        // the waiting thread may be suspended for up to SUSP ns instead of spinning on issue slots
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(parity), "r"((uint32_t)SUSP) : "memory");
+      } else {
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(a), "r"(parity) : "memory");
+      }
+      if (done) return true;
+      if (abort_flag) return false;
+      if (!SUSP && it > 32) __nanosleep(64);
     }
+    return false;
   };
 
-  int issued[NBUF], waited[NBUF];   // copies issued into / completions consumed from each buffer (thread 0)
+  if (tid >= 256) {
+    // ---- producer warp: lane 0 issues every copy of the CTA's chunk sequence
+    if (tid != 256) return;
+    int last_u[NB];
 #pragma unroll
-  for (int i = 0; i < NBUF; ++i) issued[i] = waited[i] = 0;
-  bool ok = true;
-  int it = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int b = it % NBUF;
-    const uint32_t t0 = (uint32_t)(tile << tb);
-    if (tid == 0) {
-      // the buffers written here were last read in an earlier iteration, which ended with a barrier
+    for (int i = 0; i < NB; ++i) last_u[i] = -1;
+    bool ok = true;
+    long long k = 0;
+    auto issue = [&](long long ptile, uint32_t off, uint32_t bytes) -> bool {
+      const int b = (int)(k % NB);
+      const int u = (int)(k / NB);
+      if (u > 0 && !wait_bar(&empty[b], (uint32_t)((u - 1) & 1))) return false;
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      if (it == 0) { issue(0, tile); ++issued[0]; }
-      if (NBUF == 1 && it > 0) { issue(0, tile); ++issued[0]; }
-      if (NBUF > 1 && tile + gridDim.x < ntiles) {
-        const int nb = (it + 1) % NBUF;
-        issue(nb, tile + gridDim.x);
-        ++issued[nb];
+      const uint32_t fb = smem_u32(&full[b]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(bytes) : "memory");
+      const char *src = reinterpret_cast<const char *>(X) + (size_t)ptile * TB + off;
+      const uint32_t dst = smem_u32(buf + (size_t)b * TR * ch);
+      for (uint32_t o = 0; o < bytes; o += 16384u) {
+        const uint32_t sz = (bytes - o) < 16384u ? (bytes - o) : 16384u;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst + o),
+                     "l"(src + o), "r"(sz), "r"(fb)
+                     : "memory");
       }
-      // outside terms active on this tile with their amplitudes, the tile part of the diagonal,
-      // the straddling bonds' tile bits
-      double d = P.c0 + P.bz * (0.5 * P.n - (double)__popc(t0));
-      int m = 0;
-      for (int k = nI + nS; k < nI + nS + nF; ++k)
-        if (!P.two[k] || (((t0 >> P.bi[k]) ^ (t0 >> P.bj[k])) & 1u)) {
-          const bool s1 = (t0 >> P.sb[k]) & 1u;
-          fmask[m] = P.mask[k];
-          fr[m] = (T)(s1 ? P.a1r[k] : P.a0r[k]);
-          fi[m] = (T)(s1 ? P.a1i[k] : P.a0i[k]);
-          ++m;
-          if (P.two[k]) d -= P.jz[k];
-        }
-      nfa = m;
-      dconst = (T)d;
-      unsigned long long f = 0, g = 0;
-      for (int k = 0; k < nS; ++k) {
-        if ((t0 >> P.bj[nI + k]) & 1u) f |= 1ull << k;
-        if ((t0 >> P.sb[nI + k]) & 1u) g |= 1ull << k;
+      last_u[b] = u;
+      ++k;
+      return true;
+    };
+    for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const uint32_t t0 = (uint32_t)(tile << tb);
+      ok = issue(tile, 0, TB);
+      for (int s = 0; ok && s < nS; ++s) {
+        const uint32_t tbit = (t0 >> shb[s]) & 1u;
+        const bool h = half_of(s);
+        ok = issue(tile ^ (long long)shi[s], h ? (tbit ? TB / 2 : 0u) : 0u, h ? TB / 2 : TB);
       }
-      sflip = f;
-      ssel = g;
+      for (int f = 0; ok && f < nF; ++f)
+        if (outside_active(f, t0)) ok = issue(tile ^ (long long)fhi[f], 0, TB);
     }
-    __syncthreads();
-    const bool got = mbar_wait(smem_u32(&bar[b]), (uint32_t)((it / NBUF) & 1));
-    if (tid == 0 && got) ++waited[b];
-    if (!__syncthreads_and(got)) {   // a copy did not arrive in time: every thread leaves the loop
-      ok = false;
-      break;
-    }
-    if (ROWMAJOR && slot < rp) {
-      const V *own = buf + (size_t)b * TR * ch;
-      const int nf = nfa;
-      const T dc = dconst;
-      const unsigned long long sf = sflip, sg = ssel;
-      for (uint32_t lr = slot; lr < TR; lr += rp) {
-        const uint32_t row = t0 + lr;
-        T d = dc + rdiag[lr];
-        V acc = zero16((V *)nullptr);
-        // outside terms: LIF partner loads at a time, then their sums
-        for (int f0 = 0; f0 < nf; f0 += LIF) {
-          V p[LIF];
-#pragma unroll
-          for (int u = 0; u < LIF; ++u)
-            if (f0 + u < nf) p[u] = ld_stream(X + (size_t)(row ^ fmask[f0 + u]) * ch + c);
-#pragma unroll
-          for (int u = 0; u < LIF; ++u)
-            if (f0 + u < nf) {
-              if constexpr (CPLX) caxpy(acc, fr[f0 + u], fi[f0 + u], p[u]);
-              else axpy(acc, fr[f0 + u], p[u]);
-            }
+    if (!ok) abort_flag = 1;
+    // drain: every buffer's last copy has landed before the CTA releases its shared memory
+    for (int b = 0; b < NB; ++b)
+      if (last_u[b] >= 0) {
+        const uint32_t a = smem_u32(&full[b]);
+        bool got = false;
+        for (int it = 0; it < (1 << 22) && !got; ++it) {
+          uint32_t done;
+          asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                       : "=r"(done) : "r"(a), "r"((uint32_t)(last_u[b] & 1)) : "memory");
+          got = done != 0;
+          if (!got && it > 32) __nanosleep(64);
         }
-        for (int k = 0; k < nS; ++k)
-          if (((lr >> slo[k]) ^ (uint32_t)(sf >> k)) & 1u) {
-            d -= sjz[k];
-            const V pv = ld_stream(X + (size_t)(row ^ smask[k]) * ch + c);
-            if constexpr (CPLX) {
-              const bool s1 = sselin[k] ? ((lr >> ssb[k]) & 1u) : ((sg >> k) & 1u);
-              caxpy(acc, s1 ? s1r[k] : s0r[k], s1 ? s1i[k] : s0i[k], pv);
-            } else {
-              axpy(acc, s0r[k], pv);
-            }
-          }
-        unsigned long long am = rmask[lr];
-        while (am) {
-          const int k = __ffsll((long long)am) - 1;
-          am &= am - 1;
-          const V pv = own[(size_t)(lr ^ imask[k]) * ch + c];
-          if constexpr (CPLX) {
-            const bool s1 = (lr >> isb[k]) & 1u;
-            caxpy(acc, s1 ? i1r[k] : i0r[k], s1 ? i1i[k] : i0i[k], pv);
-          } else {
-            axpy(acc, i0r[k], pv);
-          }
-        }
-        axpy(acc, d, own[(size_t)lr * ch + c]);
-        __stcs(Y + (size_t)row * ch + c, acc);   // streaming: keep V, not Y, in L2
+        ok = ok && got;
       }
+    if (!ok && status) atomicOr(status, ST_TIMEOUT);
+    return;
+  }
+
+  // ---- consumer warps: thread (slot, c) owns word c of rows slot + i rp of every tile
+  const int rp = 256 / ch;
+  const int slot = tid / ch, c = tid - slot * ch;
+  const bool active_thread = slot < rp;
+  const int lane = tid & 31;
+  bool ok = true;
+  long long k = 0;
+  auto take = [&]() -> const V * {   // wait for chunk k; returns its buffer (null for the whole warp on a timeout)
+    const int b = (int)(k % NB);
+    const bool got = wait_bar(&full[b], (uint32_t)((k / NB) & 1));
+    if (!__all_sync(0xffffffffu, got)) return nullptr;
+    return buf + (size_t)b * TR * ch;
+  };
+  auto release = [&]() {
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&empty[k % NB])) : "memory");
+    ++k;
+  };
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint32_t t0 = (uint32_t)(tile << tb);
+    // tile-level parts: the diagonal's constant and outside shares, the straddling bonds' tile bits
+    double dcd = P.c0 + P.bz * (0.5 * P.n - (double)__popc(t0));
+    for (int f = 0; f < nF; ++f)
+      if (ftwo[f] && outside_active(f, t0)) dcd -= P.jz[nI + nS + f];
+    const T dc = (T)dcd;
+    unsigned long long sf = 0, sg = 0;
+    for (int s = 0; s < nS; ++s) {
+      sf |= (unsigned long long)((t0 >> shb[s]) & 1u) << s;
+      sg |= (unsigned long long)((t0 >> ssb[s]) & 1u) << s;
     }
-    if (!ROWMAJOR && slot < rp) {
-      const V *own = buf + (size_t)b * TR * ch;
-      const int nf = nfa;
-      const T dc = dconst;
-      const unsigned long long sf = sflip, sg = ssel;
-      // rows of this thread in the tile: lr_i = slot + i rp, i < RPT
-      V acc[RPT];
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) acc[i] = zero16((V *)nullptr);
-      // outside terms, term by term: the partner rows of all the thread's rows are one group of
-      // independent loads (two terms per iteration: up to 2 RPT loads in flight per thread)
-      const size_t step = (size_t)rp * ch;
-#pragma unroll 2
-      for (int f = 0; f < nf; ++f) {
-        // partner of row t0 + lr is (t0 + lr) ^ m = (t0 ^ m) + lr (m has no bits below tb): the
-        // partner tile starts at row t0 ^ m, which is below N
-        const V *xp = X + ((size_t)(t0 ^ fmask[f]) + (size_t)slot) * ch + c;
-        const T ar = fr[f], ai = fi[f];
-        V p[RPT];
-#pragma unroll
-        for (int i = 0; i < RPT; ++i)
-          if (slot + i * rp < (int)TR) p[i] = ld_stream(xp + i * step);
-#pragma unroll
-        for (int i = 0; i < RPT; ++i)
-          if (slot + i * rp < (int)TR) {
-            if constexpr (CPLX) caxpy(acc[i], ar, ai, p[i]);
-            else axpy(acc[i], ar, p[i]);
-          }
-      }
+    V acc[RPT];
+    // own tile: diagonal and in-tile terms
+    const V *own = take();
+    if (!own) { ok = false; break; }
+    if (active_thread) {
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const uint32_t lr = (uint32_t)(slot + i * rp);
+        acc[i] = zero16((V *)nullptr);
         if (lr >= TR) continue;
-        const uint32_t row = t0 + lr;
         T d = dc + rdiag[lr];
-        // straddling bonds: active when the row's low bit differs from the tile's high bit
-        for (int k = 0; k < nS; ++k)
-          if (((lr >> slo[k]) ^ (uint32_t)(sf >> k)) & 1u) {
-            d -= sjz[k];
-            const V pv = ld_stream(X + (size_t)(row ^ smask[k]) * ch + c);
-            if constexpr (CPLX) {
-              const bool s1 = sselin[k] ? ((lr >> ssb[k]) & 1u) : ((sg >> k) & 1u);
-              caxpy(acc[i], s1 ? s1r[k] : s0r[k], s1 ? s1i[k] : s0i[k], pv);
-            } else {
-              axpy(acc[i], s0r[k], pv);
-            }
-          }
-        // in-tile terms from shared memory
+        for (int s = 0; s < nS; ++s)
+          if (((lr >> slo[s]) ^ (uint32_t)(sf >> s)) & 1u) d -= sjz[s];
+        V a = zero16((V *)nullptr);
+        axpy(a, d, own[(size_t)lr * ch + c]);
         unsigned long long am = rmask[lr];
         while (am) {
-          const int k = __ffsll((long long)am) - 1;
+          const int q = __ffsll((long long)am) - 1;
           am &= am - 1;
-          const V pv = own[(size_t)(lr ^ imask[k]) * ch + c];
+          const V pv = own[(size_t)(lr ^ imask[q]) * ch + c];
           if constexpr (CPLX) {
-            const bool s1 = (lr >> isb[k]) & 1u;
-            caxpy(acc[i], s1 ? i1r[k] : i0r[k], s1 ? i1i[k] : i0i[k], pv);
+            const bool s1 = (lr >> isb[q]) & 1u;
+            caxpy(a, s1 ? i1r[q] : i0r[q], s1 ? i1i[q] : i0i[q], pv);
           } else {
-            axpy(acc[i], i0r[k], pv);
+            axpy(a, i0r[q], pv);
           }
         }
-        axpy(acc[i], d, own[(size_t)lr * ch + c]);
-        __stcs(Y + (size_t)row * ch + c, acc[i]);
+        acc[i] = a;
       }
     }
-    __syncthreads();   // buffer b and the per-tile lists are free again
-  }
-  // drain: no copy may still be in flight when the CTA releases its shared memory
-  if (tid == 0) {
-    for (int i = 0; i < NBUF; ++i)
-      while (waited[i] < issued[i]) {
-        const bool got = mbar_wait(smem_u32(&bar[i]), (uint32_t)(waited[i] & 1));
-        ++waited[i];
-        ok = ok && got;
+    release();
+    // straddling bonds: active on the rows whose bit slo differs from the tile's bit
+    for (int s = 0; s < nS; ++s) {
+      const V *pb = take();
+      if (!pb) { ok = false; break; }
+      if (active_thread) {
+        const uint32_t tbit = (uint32_t)(sf >> s) & 1u, lo = slo[s];
+        const uint32_t base = (lo == (uint32_t)(tb - 1) && tbit) ? TR / 2 : 0u;
+        const bool selin = ssel_in[s];
+        const bool sgt = (sg >> s) & 1u;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const uint32_t lr = (uint32_t)(slot + i * rp);
+          if (lr >= TR || !(((lr >> lo) ^ tbit) & 1u)) continue;
+          const V pv = pb[(size_t)((lr ^ (1u << lo)) - base) * ch + c];
+          if constexpr (CPLX) {
+            const bool s1 = selin ? ((lr >> ssb[s]) & 1u) : sgt;
+            caxpy(acc[i], s1 ? s1r[s] : s0r[s], s1 ? s1i[s] : s0i[s], pv);
+          } else {
+            axpy(acc[i], s0r[s], pv);
+          }
+        }
       }
+      release();
+    }
+    if (!ok) break;
+    // outside terms active on this tile: the whole partner tile, one amplitude
+    for (int f = 0; f < nF; ++f) {
+      if (!outside_active(f, t0)) continue;
+      const V *pb = take();
+      if (!pb) { ok = false; break; }
+      if (active_thread) {
+        const bool s1 = (t0 >> fsb[f]) & 1u;
+        const T ar = s1 ? f1r[f] : f0r[f], ai = s1 ? f1i[f] : f0i[f];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+          const uint32_t lr = (uint32_t)(slot + i * rp);
+          if (lr >= TR) continue;
+          if constexpr (CPLX) caxpy(acc[i], ar, ai, pb[(size_t)lr * ch + c]);
+          else axpy(acc[i], ar, pb[(size_t)lr * ch + c]);
+        }
+      }
+      release();
+    }
+    if (!ok) break;
+    if (active_thread) {
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const uint32_t lr = (uint32_t)(slot + i * rp);
+        if (lr < TR) __stcs(Y + (size_t)(t0 + lr) * ch + c, acc[i]);
+      }
+    }
   }
-  if (!ok && status) atomicOr(status, ST_TIMEOUT);
+  if (!ok) {
+    abort_flag = 1;
+    if (status && lane == 0) atomicOr(status, ST_TIMEOUT);
+  }
+}
+
+template <typename T>
+size_t hv7_smem_bytes(int tb, int ch, int nb) {
+  const size_t TR = (size_t)1 << tb;
+  return (size_t)nb * TR * ch * 16 + TR * (8 + sizeof(T));
 }
 
 // ---------------------------------------------------------------- launcher
-constexpr int HV6_RPT = 8;   // rows per thread and tile at the launcher's tile sizes (see hv6_tile_bits)
-// the configuration the library launches (measured best of row/term order, 1-2 own-tile buffers,
-// 4-8 loads in flight and 2-6 CTAs per SM at n = 18 and 20): row-major, one own-tile buffer per
-// CTA (the 5 CTAs of an SM overlap each other's copies), 6 outside partner loads in flight per
-// thread, 5 CTAs per SM
-constexpr int HV6_NBUF = 1, HV6_LIF = 6, HV6_MINB = 5;
-constexpr bool HV6_ROWMAJOR = true;
+constexpr int HV_RPT = 8;   // rows per thread and tile at the launcher's tile sizes (see hv_tile_bits)
+// the configuration the library launches (measured best of 1-6 tile buffers and 1-6 CTAs per SM,
+// 16 and 32 KB tiles, at n = 14..20 in both precisions): 32 KB tiles, two buffers per CTA, three
+// CTAs per SM, waits that suspend the thread for up to 2 us per poll
+constexpr int HV_NB = 2, HV_MINB = 3, HV_SUSP = 2000;
 
 template <typename T, bool CPLX>
-constexpr auto hv6_product = hv6_kernel<T, HV6_NBUF, HV6_RPT, CPLX, HV6_ROWMAJOR, HV6_LIF, HV6_MINB>;
-
-template <typename T>
-size_t hv6_smem_bytes(int tb, int ch, int nbuf) {
-  const size_t TR = (size_t)1 << tb;
-  return (size_t)nbuf * TR * ch * 16 + TR * (8 + sizeof(T));
-}
+constexpr auto hv_product = hv7_kernel<T, HV_NB, HV_RPT, CPLX, HV_MINB, HV_SUSP>;
 
 namespace {
-int g_hv6_occ[2][2] = {{0, 0}, {0, 0}};   // [fp64][cplx]: CTAs per SM of the product kernel
+int g_hv_occ[2][2] = {{0, 0}, {0, 0}};   // [fp64][cplx]: CTAs per SM of the product kernel
 }  // namespace
 
 // Tile bits for a row of `rowb` bytes: about 32 KB of rows per tile, at most all N rows.
-static int hv6_tile_bits(int n, size_t rowb) {
+static int hv_tile_bits(int n, size_t rowb) {
   int tb = 0;
   while (((size_t)2 << tb) * rowb <= 32768) ++tb;
   return tb < n ? tb : n;
 }
 
-int hv6_init() {
+int hv_tiled_init() {
   const int lim = 200 * 1024;
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {
     const cudaError_t x = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (x != cudaSuccess) e = x;
   };
-  set((const void *)hv6_product<float, false>);
-  set((const void *)hv6_product<double, false>);
-  set((const void *)hv6_product<float, true>);
-  set((const void *)hv6_product<double, true>);
+  set((const void *)hv_product<float, false>);
+  set((const void *)hv_product<double, false>);
+  set((const void *)hv_product<float, true>);
+  set((const void *)hv_product<double, true>);
   if (e != cudaSuccess) return -1;
   // occupancy at the standard tile size (32 KB per tile buffer)
   int o = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<float, false>, 256, hv6_smem_bytes<float>(8, 8, HV6_NBUF));
-  g_hv6_occ[0][0] = o > 0 ? o : 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<float, true>, 256, hv6_smem_bytes<float>(8, 8, HV6_NBUF));
-  g_hv6_occ[0][1] = o > 0 ? o : 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<double, false>, 256, hv6_smem_bytes<double>(7, 16, HV6_NBUF));
-  g_hv6_occ[1][0] = o > 0 ? o : 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv6_product<double, true>, 256, hv6_smem_bytes<double>(7, 16, HV6_NBUF));
-  g_hv6_occ[1][1] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv_product<float, false>, 288, hv7_smem_bytes<float>(8, 8, HV_NB));
+  g_hv_occ[0][0] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv_product<float, true>, 288, hv7_smem_bytes<float>(8, 8, HV_NB));
+  g_hv_occ[0][1] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv_product<double, false>, 288, hv7_smem_bytes<double>(7, 16, HV_NB));
+  g_hv_occ[1][0] = o > 0 ? o : 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, hv_product<double, true>, 288, hv7_smem_bytes<double>(7, 16, HV_NB));
+  g_hv_occ[1][1] = o > 0 ? o : 1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // The terms of the model sorted for a tile size (tile_bits > 0 overrides the 32 KB default).
-// Returns false when hv6 does not apply: row bytes not a multiple of 16, fewer than 16 rows per
+// Returns false when the tiled kernel does not apply: row bytes not a multiple of 16, fewer than 16 rows per
 // tile, or more than 64 terms inside a tile.
-bool hv6_plan(bool fp64, const ModelArgs &M, long long N, int r, int tile_bits, HvPlan *Pout) {
+bool hv_plan(bool fp64, const ModelArgs &M, long long N, int r, int tile_bits, HvPlan *Pout) {
   const size_t rowb = (size_t)r * (fp64 ? 16 : 8);
   if (rowb % 16 != 0 || rowb / 16 > 256) return false;
-  int tb = tile_bits > 0 ? (tile_bits < M.n ? tile_bits : M.n) : hv6_tile_bits(M.n, rowb);
+  int tb = tile_bits > 0 ? (tile_bits < M.n ? tile_bits : M.n) : hv_tile_bits(M.n, rowb);
   const int rp = 256 / (int)(rowb / 16);
-  while (tb > 0 && (((1 << tb) + rp - 1) / rp) > HV6_RPT) --tb;   // every row of a tile has a thread
+  while (tb > 0 && (((1 << tb) + rp - 1) / rp) > HV_RPT) --tb;   // every row of a tile has a thread
   if (tb < 4 || M.nb > MAX_BONDS) return false;
   // the terms: the bonds, then (with a transverse field) one one-bit flip per spin
   const bool field = M.cplx && (M.bx != 0.0 || M.by != 0.0);
@@ -470,24 +499,24 @@ bool hv6_plan(bool fp64, const ModelArgs &M, long long N, int r, int tile_bits, 
 }
 
 // Returns true when the launch was made; false when the caller must use another kernel.
-bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
-                int *status, int tile_bits) {
+bool launch_hv_tiled(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm,
+                     cudaStream_t st, int *status, int tile_bits) {
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Y) & 15) || X == Y) return false;
   HvPlan P;
-  if (!hv6_plan(fp64, M, N, r, tile_bits, &P)) return false;
-  const size_t smem = fp64 ? hv6_smem_bytes<double>(P.tb, P.ch, HV6_NBUF) : hv6_smem_bytes<float>(P.tb, P.ch, HV6_NBUF);
+  if (!hv_plan(fp64, M, N, r, tile_bits, &P)) return false;
+  const size_t smem = fp64 ? hv7_smem_bytes<double>(P.tb, P.ch, HV_NB) : hv7_smem_bytes<float>(P.tb, P.ch, HV_NB);
   if (smem > 200 * 1024) return false;
-  const int occ = g_hv6_occ[fp64 ? 1 : 0][M.cplx ? 1 : 0];
+  const int occ = g_hv_occ[fp64 ? 1 : 0][M.cplx ? 1 : 0];
   const long long ntiles = N >> P.tb;
   const long long cap = (long long)(occ > 0 ? occ : 1) * nsm;
   const int grid = (int)(ntiles < cap ? ntiles : cap);
   ::lrei::count_launch();
   if (fp64) {
-    auto kern = M.cplx ? hv6_product<double, true> : hv6_product<double, false>;
-    kern<<<grid, 256, smem, st>>>(P, reinterpret_cast<const double2 *>(X), reinterpret_cast<double2 *>(Y), status);
+    auto kern = M.cplx ? hv_product<double, true> : hv_product<double, false>;
+    kern<<<grid, 288, smem, st>>>(P, reinterpret_cast<const double2 *>(X), reinterpret_cast<double2 *>(Y), status);
   } else {
-    auto kern = M.cplx ? hv6_product<float, true> : hv6_product<float, false>;
-    kern<<<grid, 256, smem, st>>>(P, reinterpret_cast<const float4 *>(X), reinterpret_cast<float4 *>(Y), status);
+    auto kern = M.cplx ? hv_product<float, true> : hv_product<float, false>;
+    kern<<<grid, 288, smem, st>>>(P, reinterpret_cast<const float4 *>(X), reinterpret_cast<float4 *>(Y), status);
   }
   return true;
 }

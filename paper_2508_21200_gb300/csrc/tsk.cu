@@ -911,7 +911,7 @@ void launch_reduce(const double *partial, int nparts, int len_doubles, double *o
 
 void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                int *status) {
-  if (launch_hv6(fp64, M, X, Y, N, r, nsm, st, status)) return;
+  if (launch_hv_tiled(fp64, M, X, Y, N, r, nsm, st, status)) return;
   // rows that are not a multiple of 16 bytes, or fewer than 16 rows: the per-row gather
   auto grid_for = [&](int cpt) {
     long long total = N * (r / cpt);
@@ -1081,7 +1081,7 @@ void launch_check_finite(bool fp64, const void *X, long long N, int r, int *stat
 namespace lrei {
 // Raise the dynamic shared-memory limit of every tile kernel once (outside any stream capture).
 int ts_init() {
-  if (hv6_init()) return -1;
+  if (hv_tiled_init()) return -1;
   const int lim = 210 * 1024;
   cudaError_t e = cudaSuccess;
   auto set = [&](const void *f) {

@@ -44,9 +44,10 @@ void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long 
 
 // Full-row matrix-free H.V (hv.cu): returns false when the layout does not apply.
 // tile_bits > 0 overrides the tile size (rows = 2^tile_bits), else about 32 KB per tile.
-bool launch_hv6(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
+bool launch_hv_tiled(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                 int *status, int tile_bits = 0);
-int hv6_init();
+int hv_tiled_init();
+
 
 // Observable Grams of V (N x r): blocks (column-major r x r each, complex double):
 //   0: V^*HV  1: (HV)^*(HV)  2: V^*V  3: V^* Mx V  4: V^* My V  5: V^* Mz V
