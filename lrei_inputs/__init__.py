@@ -16,12 +16,15 @@ draw order is bond anisotropies, then the initial factor V, then Lambda.
 from __future__ import annotations
 
 import dataclasses
+import json
+import os
+
 import numpy as np
 
 __all__ = [
     "Bonds", "chain_bonds", "triangular_bonds", "haar_orthonormal", "dirichlet_spectrum",
     "basis_state", "af1_state", "af2_state", "ghz_state", "w_state",
-    "Workload", "workload", "rng_for",
+    "Workload", "workload", "rng_for", "load_config",
 ]
 
 
@@ -147,45 +150,55 @@ class Workload:
     lam: np.ndarray | None = None
 
 
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "configs")
+
+
+def load_config(config: int) -> dict:
+    """The recipe of workload `config` from configs/cfg<config>.json."""
+    with open(os.path.join(CONFIG_DIR, f"cfg{config}.json")) as f:
+        return json.load(f)
+
+
 def workload(config: int, traj: int = 0, *, n: int | None = None, r: int | None = None,
              kappa: float | None = None, model: str | None = None, scheme: str | None = None,
              with_state: bool = True) -> Workload:
-    """The synthetic workloads.
+    """The synthetic workloads, from the recipes in configs/cfg1.json .. cfg5.json.
 
     1: open chain n=8, r=4, J=1, B_z=0.5, kappa=0.1, q-LL, RK4, dt=0.01, 1000 steps.
     2: periodic chain n=16, r=8, Jxy=1, Jz=1+U[-0.2,0.2] per bond, B_z=1, dt=0.005, 500 steps.
     3: open chain n=20, r=16, J=1, B_z=0.5, kappa=0.1, RK4, dt=0.01, 100 steps.
     4: open chains n in U{10..18}, r in U{2..16}, kappa log-uniform in [1e-3, 1], RK4, dt=0.01, 200 steps.
     5: open chain n=22, r=32, kappa=0.05, J=1, B_z=0.5, 50 steps (controller evaluation).
-    Keyword overrides let tests shrink a workload while keeping its recipe.
+    Keyword overrides let tests shrink a workload while keeping its recipe.  Draw order per seed:
+    n, r, kappa (where the recipe gives ranges), the bond anisotropies, then V, then Lambda.
     """
-    rng = rng_for(config, traj)
-    if config == 1:
-        nn, rr, bonds, B, kap, mdl, sch, dt, steps = 8, 4, None, (0.0, 0.0, 0.5), 0.1, "qll", "rk4", 0.01, 1000
-        nn = n or nn
-        bonds = chain_bonds(nn, periodic=False)
-    elif config == 2:
-        nn = n or 16
-        m = nn if nn > 2 else nn - 1
-        aniso = rng.uniform(-0.2, 0.2, size=m)
-        bonds = chain_bonds(nn, periodic=True, aniso=aniso)
-        rr, B, kap, mdl, sch, dt, steps = 8, (0.0, 0.0, 1.0), 0.1, "qll", "rk4", 0.005, 500
-    elif config == 3:
-        nn = n or 20
-        bonds = chain_bonds(nn, periodic=False)
-        rr, B, kap, mdl, sch, dt, steps = 16, (0.0, 0.0, 0.5), 0.1, "qll", "rk4", 0.01, 100
-    elif config == 4:
-        nn = n or int(rng.integers(10, 19))
-        rr = r or int(rng.integers(2, 17))
-        kap = kappa if kappa is not None else float(10.0 ** rng.uniform(-3.0, 0.0))
-        bonds = chain_bonds(nn, periodic=False)
-        B, mdl, sch, dt, steps = (0.0, 0.0, 0.5), "qll", "rk4", 0.01, 200
-    elif config == 5:
-        nn = n or 22
-        bonds = chain_bonds(nn, periodic=False)
-        rr, B, kap, mdl, sch, dt, steps = 32, (0.0, 0.0, 0.5), 0.05, "qll", "rk4", 0.01, 50
-    else:
+    if config not in (1, 2, 3, 4, 5):
         raise ValueError(f"unknown workload {config}")
+    cfg = load_config(config)
+    lat = cfg["lattice"]
+    rng = rng_for(config, traj)
+    if "n_range" in lat:
+        lo, hi = lat["n_range"]
+        nn = n or int(rng.integers(lo, hi + 1))
+    else:
+        nn = n or int(lat["n"])
+    if "r_range" in cfg:
+        lo, hi = cfg["r_range"]
+        rr = r or int(rng.integers(lo, hi + 1))
+    else:
+        rr = int(cfg["r"])
+    if "kappa_log10_range" in cfg:
+        lo, hi = cfg["kappa_log10_range"]
+        kap = kappa if kappa is not None else float(10.0 ** rng.uniform(lo, hi))
+    else:
+        kap = float(cfg["kappa"])
+    aniso = None
+    if lat.get("jz_aniso"):
+        m = nn if (lat["periodic"] and nn > 2) else nn - 1
+        aniso = rng.uniform(lat["jz_aniso"][0], lat["jz_aniso"][1], size=m)
+    bonds = chain_bonds(nn, periodic=bool(lat["periodic"]), J=float(lat["jxy"]), aniso=aniso)
+    B = tuple(float(x) for x in cfg["B"])
+    mdl, sch, dt, steps = cfg["model"], cfg["scheme"], float(cfg["dt"]), int(cfg["steps"])
     rr = r or rr
     kap = kappa if kappa is not None else kap
     mdl = model or mdl

@@ -35,6 +35,8 @@ void launch_rdm_final(const double *partial, int nparts, int npairs, double p_we
 // controller network inference on a given stream (mlp.cu)
 int lrei_mlp_forward_on(lrei_mlp *net, const float *X, int B, float *Y, cudaStream_t st);
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -49,6 +51,16 @@ namespace lrei {
 static std::atomic<long long> g_launches{0};
 long long launch_counter() { return g_launches.load(); }
 void count_launch(int n) { g_launches += n; }
+
+// A named NVTX range for the duration of one ABI call (shows in Nsight timelines; no cost when
+// no tool is attached).  Work inside a captured step graph is not split into ranges: the graph
+// replays without host code.
+struct NvtxScope {
+  explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope &) = delete;
+  NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 int cuda_fail(cudaError_t e, const char *what) {
   (void)what;
@@ -1617,6 +1629,7 @@ int lrei_destroy(lrei_ctx *c) {
 }
 
 int lrei_set_state(lrei_ctx *c, const void *V_dev, int r, int ld, int dtype, const double *Lambda_host) {
+  NvtxScope nvtx_scope("lrei_set_state");
   if (!c || !V_dev || !Lambda_host) return LREI_ERR_ARG;
   if (r < 1 || r > c->r_max || ld < r || (dtype != LREI_C128 && dtype != LREI_C64)) return LREI_ERR_ARG;
   double sum = 0.0;
@@ -1698,6 +1711,7 @@ int lrei_get_state(lrei_ctx *c, void *V_dev_out, double *Lambda_host_out, double
 }
 
 int lrei_step(lrei_ctx *c, double dt, lrei_scheme scheme, int nsteps) {
+  NvtxScope nvtx_scope("lrei_step");
   if (!c) return LREI_ERR_ARG;
   if (!c->has_state) return LREI_ERR_STATE;
   if (!std::isfinite(dt) || nsteps < 0) return LREI_ERR_ARG;
@@ -1744,6 +1758,7 @@ int lrei_step(lrei_ctx *c, double dt, lrei_scheme scheme, int nsteps) {
 }
 
 int lrei_step_adaptive(lrei_ctx *c, double t_end, double tol, int controller) {
+  NvtxScope nvtx_scope("lrei_step_adaptive");
   if (!c) return LREI_ERR_ARG;
   if (!c->has_state) return LREI_ERR_STATE;
   if (!std::isfinite(t_end) || !(tol > 0) || (controller != 0 && controller != 1)) return LREI_ERR_ARG;
@@ -1798,6 +1813,7 @@ int lrei_controller_records(lrei_ctx *c, double *rows, int max_rows, int *n_rows
 }
 
 int lrei_observables(lrei_ctx *c, lrei_obs *out) {
+  NvtxScope nvtx_scope("lrei_observables");
   if (!c || !out) return LREI_ERR_ARG;
   if (!c->has_state) return LREI_ERR_STATE;
   const int r = c->r;
@@ -2059,6 +2075,7 @@ int lrei_householder(lrei_ctx *c, void *U_dev, double *T_host, double *D_host) {
 
 int lrei_two_spin_rdm(lrei_ctx *c, int npairs, const int *site_k, const int *site_l, double *R_host,
                       double *concurrence_host, double *negativity_host) {
+  NvtxScope nvtx_scope("lrei_two_spin_rdm");
   if (!c || npairs < 1 || npairs > LREI_RDM_MAX_PAIRS || !site_k || !site_l) return LREI_ERR_ARG;
   if (!c->has_state) return LREI_ERR_STATE;
   if (c->n < 2) return LREI_ERR_ARG;
@@ -2116,6 +2133,7 @@ int lrei_two_spin_rdm(lrei_ctx *c, int npairs, const int *site_k, const int *sit
 }
 
 int lrei_truncate_rank(lrei_ctx *c, double tol_r, int *r_out, double *dropped_out) {
+  NvtxScope nvtx_scope("lrei_truncate_rank");
   if (!c || !std::isfinite(tol_r) || tol_r < 0.0) return LREI_ERR_ARG;
   if (!c->has_state) return LREI_ERR_STATE;
   const int r = c->r;
@@ -2180,6 +2198,7 @@ long long lrei_checkpoint_bytes(lrei_ctx *c) {
 }
 
 int lrei_checkpoint_save(lrei_ctx *c, void *buf, long long bytes) {
+  NvtxScope nvtx_scope("lrei_checkpoint_save");
   if (!c || !buf) return LREI_ERR_ARG;
   if (!c->has_state) return LREI_ERR_STATE;
   if (bytes < (long long)ckpt_bytes(c)) return LREI_ERR_ARG;
@@ -2227,6 +2246,7 @@ int lrei_checkpoint_save(lrei_ctx *c, void *buf, long long bytes) {
 }
 
 int lrei_checkpoint_load(lrei_ctx *c, const void *buf, long long bytes) {
+  NvtxScope nvtx_scope("lrei_checkpoint_load");
   if (!c || !buf || bytes < (long long)sizeof(CkptHeader)) return LREI_ERR_ARG;
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
@@ -2379,12 +2399,14 @@ int lrei_batch_create(int nctx, lrei_ctx *const *ctxs, void *cuda_stream, lrei_b
 }
 
 int lrei_batch_step(lrei_batch *b, double dt, int nsteps) {
+  NvtxScope nvtx_scope("lrei_batch_step");
   if (!b || !std::isfinite(dt) || nsteps < 0) return LREI_ERR_ARG;
   if (nsteps == 0) return LREI_OK;
   return batch_run(b, dt, nsteps);
 }
 
 int lrei_batch_autotune(lrei_batch *b, double dt, int steps, int *nsm_out, double *ms_out) {
+  NvtxScope nvtx_scope("lrei_batch_autotune");
   if (!b || !std::isfinite(dt) || steps < 1) return LREI_ERR_ARG;
   const int nsm = b->ctx[0]->nsm;
   int best = nsm;
