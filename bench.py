@@ -564,6 +564,89 @@ def run_batch_leg(count, steps):
         return {"error": str(e)[:200]}
 
 
+def run_workload5(args):
+    """Workload 5: the controller evaluation at the largest size (open chain n=22, r=32,
+    kappa=0.05, complex64 bulk).  The network is trained on plain-controller data from chains
+    n = 12..18 at r=32, then the n=22 run is integrated adaptively over 50 dt-equivalent steps
+    (T = 0.5) by the plain rule and by the learned rule, each against a reference at dt/4; the
+    fixed-dt mixed and FP64 step rates are measured beside them.  One JSON line."""
+    import numpy as np
+    import torch
+    import lrei_inputs as li
+    from paper_2508_21200_gb300 import Lrei, controller as ctl
+    w = li.workload(5)
+    stream = torch.cuda.current_stream()
+
+    def make(prec):
+        L = Lrei(w.n, w.bonds, w.B, w.kappa, w.model, prec, w.r)
+        L.set_state(torch.from_numpy(w.V).to("cuda", torch.complex128 if prec == "fp64" else torch.complex64), w.lam)
+        return L
+
+    def timed(L, dt, k):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        L.step(dt, "rk4", k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+    sE = float(np.sum(np.abs(w.bonds.jxy) + np.abs(w.bonds.jz) / 2) + w.n * np.linalg.norm(w.B) / 2)
+    scales = {"energy": sE, "mx": 0.5, "my": 0.5, "mz": 0.5, "purity": 1.0, "trace": 1.0}
+
+    def obs_err(o, ref):
+        return max(abs(o[k] - ref[k]) / max(abs(ref[k]), s) for k, s in scales.items())
+    T, n_ad = w.steps * w.dt, w.steps
+    Lm = make("mixed")
+    Lm.step(w.dt, "rk4", 2)
+    Lm.set_state(torch.from_numpy(w.V).to("cuda", torch.complex64), w.lam)
+    ms_mixed = timed(Lm, w.dt, w.steps)
+    om = Lm.observables()
+    del Lm
+    Ld = make("fp64")
+    Ld.step(w.dt, "rk4", 1)
+    ms_fp64 = timed(Ld, w.dt, 2)
+    del Ld
+    Lr = make("mixed")
+    Lr.step(w.dt / 4, "rk4", 4 * w.steps)
+    oref = Lr.observables()
+    del Lr
+    cfg = li.load_config(5)
+    lo, hi = cfg["train_n_range"]
+    train_w = [li.workload(4, t, n=n, r=w.r, kappa=w.kappa) for t, n in enumerate(range(lo, hi + 1, 2))]
+    t_tr = time.perf_counter()
+    Xtr, Ytr = ctl.generate(train_w, t_end=0.4, tols=(1e-4, 3e-5, 1e-5), precision="mixed")
+    net, tr_loss = ctl.fit(Xtr, Ytr, iters=2000, lr=2e-3)
+    t_tr = time.perf_counter() - t_tr
+    tol = max(args.tol, 5e-6)
+
+    def adaptive(controller):
+        L = make("mixed")
+        L.controller_config(judge_every=args.judge_every, record=False, h0=w.dt)
+        if controller == 1:
+            L.controller_attach(net)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.step_adaptive(T, tol, controller)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        res = {"wall_ms": round(wall * 1e3, 1), "controller_stats": L.controller_stats(),
+               "obs_rel_err_vs_reference": obs_err(L.observables(), oref),
+               "equiv_steps_per_s": round(n_ad / wall, 3)}
+        del L
+        return res
+    plain, learned = adaptive(0), adaptive(1)
+    print(json.dumps({
+        "workload": f"open chain n={w.n} r={w.r} J=1 Bz=0.5 kappa={w.kappa} q-LL, T={T:g} (50 dt-equivalent RK4 steps)",
+        "mixed_fixed_dt": {"steps_per_s": round(1000.0 / ms_mixed, 3), "ms_per_step": round(ms_mixed, 3),
+                           "obs_rel_err_vs_reference": obs_err(om, oref)},
+        "fp64_gpu": {"steps_per_s": round(1000.0 / ms_fp64, 3), "ms_per_step": round(ms_fp64, 2), "steps_timed": 2},
+        "reference": "mixed path at dt/4 over the same span",
+        "train": {"workloads": f"open chains n={lo}..{hi} step 2, r={w.r}", "rows": int(Xtr.shape[0]),
+                  "loss": tr_loss, "seconds": round(t_tr, 1)},
+        "plain_rule": plain, "learned": learned, "tol_per_step": tol,
+        "gain_vs_plain_rule": round(plain["wall_ms"] / learned["wall_ms"], 3),
+        "note": "host clock around each adaptive run (graph capture of a fresh context included)"}))
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores: whole RK4 steps at the benchmark size, all cores,
     then one step on one BLAS thread.  Under torchrun only rank 0 runs it."""
@@ -627,13 +710,17 @@ def main():
                     help="time only the roofline kernels (Gram pass, H.V) at chain size --n")
     ap.add_argument("--n", type=int, default=20)
     ap.add_argument("--no-batch", action="store_true", help="skip the many-trajectory leg")
+    ap.add_argument("--workload5", action="store_true",
+                    help="only the controller evaluation at n=22, r=32 (separate JSON line)")
     ap.add_argument("--batch-trajectories", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=10)
     args = ap.parse_args()
     if args.oracle_steps:
         print(json.dumps(oracle_steps(args.oracle_warmup, args.oracle_steps, args.oracle_budget)))
         return
-    if args.kernels_only:
+    if args.workload5:
+        run_workload5(args)
+    elif args.kernels_only:
         run_kernels(args)
     elif args.impl == "reference":
         run_reference(args)

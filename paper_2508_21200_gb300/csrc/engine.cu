@@ -698,6 +698,27 @@ __global__ void x11_from_g_kernel(const zd *__restrict__ G, int ldg, int r, cons
   }
 }
 
+// The six observable Grams (column-major r x r each, in the order obs_final_kernel reads them:
+// V^*HV, (HV)^*(HV), V^*V, V^*M_xV, V^*M_yV, V^*M_zV) from the two measured blocks
+//   R1 = [HV, CV, ZV, V]^* V  (4r x r, C = M_x + i M_y, Z = M_z) and  R2 = (HV)^*(HV),
+// using that H, M_z and V^*V are Hermitian: V^*AV = (A V)^*V conjugate-transposed, and
+// V^*M_xV = (K + K^*)/2, V^*M_yV = (K - K^*)/(2i) for K = V^*CV.
+__global__ void obs_assemble_kernel(const zd *__restrict__ R1, const zd *__restrict__ R2, int r, zd *__restrict__ out) {
+  const int ld = 4 * r;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e % r, j = e / r;   // entry (i, j) of every block
+    auto blkT = [&](int m, int a, int b) { return conj(R1[(size_t)a * ld + m * r + b]); };   // (block m)^*: entry (a, b)
+    const zd K = blkT(1, i, j), Kt = blkT(1, j, i);
+    out[0 * r * r + e] = blkT(0, i, j);
+    out[1 * r * r + e] = R2[(size_t)j * r + i];
+    out[2 * r * r + e] = R1[(size_t)j * ld + 3 * r + i];
+    out[3 * r * r + e] = mk<double>(0.5 * (K.re + Kt.re), 0.5 * (K.im - Kt.im));
+    // (K - K^*)/(2i): K - conj(K^T) = (K.re - Kt.re) + i (K.im + Kt.im); divided by 2i
+    out[4 * r * r + e] = mk<double>(0.5 * (K.im + Kt.im), -0.5 * (K.re - Kt.re));
+    out[5 * r * r + e] = blkT(2, i, j);
+  }
+}
+
 void launch_obs_final(const double *red, int r, const double *lam, double *out, cudaStream_t st) {
   ::lrei::count_launch();
   obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), st>>>(red, r, lam, out, 0.0, 0.0, nullptr);
@@ -1818,8 +1839,36 @@ int lrei_observables(lrei_ctx *c, lrei_obs *out) {
   if (!c->has_state) return LREI_ERR_STATE;
   const int r = c->r;
   enter(c);
-  int g = launch_obs(c->fp64, c->M, c->V, c->N, r, c->partial, c->nsm, c->st);
-  launch_reduce(c->partial, g, 6 * r * r * 2, c->red, c->st);
+  // H V, (M_x + i M_y) V and M_z V on full rows into the idle Krylov blocks, then two measured
+  // Gram passes; where the full-row kernels do not apply, one fused gather pass
+  void *S = c->Sbuf, *CV = c->blk[0], *ZV = c->blk[1];
+  const bool tiled = launch_hv_tiled(c->fp64, c->M, c->V, S, c->N, r, c->nsm, c->st, c->status_dev) &&
+                     launch_magnetization(c->fp64, 1, c->n, c->V, CV, c->N, r, c->nsm, c->st, c->status_dev) &&
+                     launch_magnetization(c->fp64, 0, c->n, c->V, ZV, c->N, r, c->nsm, c->st, c->status_dev);
+  if (tiled) {
+    TSArgs a{};
+    a.nq = 3;
+    a.gram_left = 3;
+    a.q[0] = S;
+    a.q[1] = CV;
+    a.q[2] = ZV;
+    a.src = c->V;
+    int rc = ts_pass(c, a, c->nsm);
+    if (rc) { leave(c); return rc; }
+    zd *R1 = reinterpret_cast<zd *>(c->Uf), *R2 = R1 + 4 * r * r;   // small scratch, idle outside a step
+    LREI_CUDA_TRY(cudaMemcpyAsync(R1, c->red, (size_t)4 * r * r * sizeof(zd), cudaMemcpyDeviceToDevice, c->st));
+    TSArgs b{};
+    b.nq = 0;
+    b.gram_left = 0;
+    b.src = S;
+    if ((rc = ts_pass(c, b, c->nsm))) { leave(c); return rc; }
+    LREI_CUDA_TRY(cudaMemcpyAsync(R2, c->red, (size_t)r * r * sizeof(zd), cudaMemcpyDeviceToDevice, c->st));
+    ::lrei::count_launch();
+    obs_assemble_kernel<<<1, 256, 0, c->st>>>(R1, R2, r, reinterpret_cast<zd *>(c->red));
+  } else {
+    const int g = launch_obs(c->fp64, c->M, c->V, c->N, r, c->partial, c->nsm, c->st);
+    launch_reduce(c->partial, g, 6 * r * r * 2, c->red, c->st);
+  }
   ::lrei::count_launch();
   obs_final_kernel<<<1, 256, 4 * r * r * sizeof(zd), c->st>>>(c->red, r, c->lam0_dev, c->obs_dev, c->werner_p,
                                                                1.0 / (double)c->N, c->mu_dev);

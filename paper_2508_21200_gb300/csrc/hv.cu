@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
     double d = -P.bz * (double)__popc(lr);
     for (int k = 0; k < nI; ++k)
       if (!P.two[k] || (((lr >> P.bi[k]) ^ (lr >> P.bj[k])) & 1u)) {
-        m |= 1ull << k;
         if (P.two[k]) d -= P.jz[k];
+        // a term whose amplitude on this row is zero keeps its diagonal share but reads no partner
+        const bool s1 = (lr >> P.sb[k]) & 1u;
+        if (s1 ? (P.a1r[k] != 0.0 || P.a1i[k] != 0.0) : (P.a0r[k] != 0.0 || P.a0i[k] != 0.0)) m |= 1ull << k;
       }
     rmask[lr] = m;
     rdiag[lr] = (T)d;
@@ -186,8 +188,13 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
   // a straddling bond copies the half of its partner tile that holds the partners (rows whose
   // bit slo equals the tile's bit) when slo is the top row bit, else the whole tile
   auto half_of = [&](int s) { return (int)slo[s] == tb - 1; };
-  auto outside_active = [&](int f, uint32_t t0) {
+  auto outside_active = [&](int f, uint32_t t0) {   // the term acts on the tile (diagonal share)
     return !ftwo[f] || (((t0 >> fbi[f]) ^ (t0 >> fbj[f])) & 1u);
+  };
+  auto outside_load = [&](int f, uint32_t t0) {     // ... and its amplitude there is nonzero
+    if (!outside_active(f, t0)) return false;
+    const bool s1 = (t0 >> fsb[f]) & 1u;
+    return s1 ? (f1r[f] != (T)0 || f1i[f] != (T)0) : (f0r[f] != (T)0 || f0i[f] != (T)0);
   };
   // bounded wait that also gives up once another warp has aborted
   auto wait_bar = [&](unsigned long long *bar, uint32_t parity) -> bool {
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
         ok = issue(tile ^ (long long)shi[s], h ? (tbit ? TB / 2 : 0u) : 0u, h ? TB / 2 : TB);
       }
       for (int f = 0; ok && f < nF; ++f)
-        if (outside_active(f, t0)) ok = issue(tile ^ (long long)fhi[f], 0, TB);
+        if (outside_load(f, t0)) ok = issue(tile ^ (long long)fhi[f], 0, TB);
     }
     if (!ok) abort_flag = 1;
     // drain: every buffer's last copy has landed before the CTA releases its shared memory
@@ -354,7 +361,7 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
     if (!ok) break;
     // outside terms active on this tile: the whole partner tile, one amplitude
     for (int f = 0; f < nF; ++f) {
-      if (!outside_active(f, t0)) continue;
+      if (!outside_load(f, t0)) continue;
       const V *pb = take();
       if (!pb) { ok = false; break; }
       if (active_thread) {
@@ -498,27 +505,64 @@ bool hv_plan(bool fp64, const ModelArgs &M, long long N, int r, int tile_bits, H
   return true;
 }
 
-// Returns true when the launch was made; false when the caller must use another kernel.
-bool launch_hv_tiled(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm,
-                     cudaStream_t st, int *status, int tile_bits) {
+// One launch of the product kernel for a built plan (cplx: complex or row-dependent amplitudes).
+static bool launch_hv_plan(bool fp64, bool cplx, const HvPlan &P, const void *X, void *Y, int nsm, cudaStream_t st,
+                           int *status) {
   if ((reinterpret_cast<uintptr_t>(X) & 15) || (reinterpret_cast<uintptr_t>(Y) & 15) || X == Y) return false;
-  HvPlan P;
-  if (!hv_plan(fp64, M, N, r, tile_bits, &P)) return false;
   const size_t smem = fp64 ? hv7_smem_bytes<double>(P.tb, P.ch, HV_NB) : hv7_smem_bytes<float>(P.tb, P.ch, HV_NB);
   if (smem > 200 * 1024) return false;
-  const int occ = g_hv_occ[fp64 ? 1 : 0][M.cplx ? 1 : 0];
-  const long long ntiles = N >> P.tb;
+  const int occ = g_hv_occ[fp64 ? 1 : 0][cplx ? 1 : 0];
+  const long long ntiles = P.N >> P.tb;
   const long long cap = (long long)(occ > 0 ? occ : 1) * nsm;
   const int grid = (int)(ntiles < cap ? ntiles : cap);
   ::lrei::count_launch();
   if (fp64) {
-    auto kern = M.cplx ? hv_product<double, true> : hv_product<double, false>;
+    auto kern = cplx ? hv_product<double, true> : hv_product<double, false>;
     kern<<<grid, 288, smem, st>>>(P, reinterpret_cast<const double2 *>(X), reinterpret_cast<double2 *>(Y), status);
   } else {
-    auto kern = M.cplx ? hv_product<float, true> : hv_product<float, false>;
+    auto kern = cplx ? hv_product<float, true> : hv_product<float, false>;
     kern<<<grid, 288, smem, st>>>(P, reinterpret_cast<const float4 *>(X), reinterpret_cast<float4 *>(Y), status);
   }
   return true;
+}
+
+// Returns true when the launch was made; false when the caller must use another kernel.
+bool launch_hv_tiled(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm,
+                     cudaStream_t st, int *status, int tile_bits) {
+  HvPlan P;
+  if (!hv_plan(fp64, M, N, r, tile_bits, &P)) return false;
+  return launch_hv_plan(fp64, M.cplx != 0, P, X, Y, nsm, st, status);
+}
+
+// The magnetisation operators on full rows (Sec. 3.6, the expectation values of eq. spin_op):
+// which = 0: Y = M_z X, M_z = (1/n) sum_i S^z_i, a diagonal (n/2 - popcount(b)) / n;
+// which = 1: Y = (M_x + i M_y) X = (1/n) sum_i S^+_i X, the raising operator of each site, which
+//   maps a row b with bit i = 0 (spin up) to the partner b ^ 2^i and rows with bit i = 1 to zero.
+// Both M_x and M_y Grams follow from the one Gram C = X^*(M_x + i M_y)X: X^*M_xX = (C + C^*)/2 and
+// X^*M_yX = (C - C^*)/(2i), the two operators being Hermitian.
+bool launch_magnetization(bool fp64, int which, int n, const void *X, void *Y, long long N, int r, int nsm,
+                          cudaStream_t st, int *status) {
+  ModelArgs M;
+  std::memset(&M, 0, sizeof(M));
+  M.n = n;
+  if (which == 0) {
+    M.bz = 1.0 / n;
+  } else {
+    M.cplx = 1;
+    M.bx = 1.0;   // gives one one-bit term per site; the amplitudes are set below
+  }
+  HvPlan P;
+  if (!hv_plan(fp64, M, N, r, 0, &P)) return false;
+  if (which == 1) {
+    const int nt = P.nI + P.nS + P.nF;
+    for (int k = 0; k < nt; ++k) {
+      P.a0r[k] = 1.0 / n;   // output row with the bit up: the partner's amplitude
+      P.a0i[k] = 0.0;
+      P.a1r[k] = 0.0;
+      P.a1i[k] = 0.0;
+    }
+  }
+  return launch_hv_plan(fp64, which == 1, P, X, Y, nsm, st, status);
 }
 
 }  // namespace lrei

@@ -47,6 +47,10 @@ void launch_hv(bool fp64, const ModelArgs &M, const void *X, void *Y, long long 
 bool launch_hv_tiled(bool fp64, const ModelArgs &M, const void *X, void *Y, long long N, int r, int nsm, cudaStream_t st,
                 int *status, int tile_bits = 0);
 int hv_tiled_init();
+// Y = M_z X (which = 0) or Y = (M_x + i M_y) X (which = 1) on full rows (hv.cu); false when the
+// layout does not apply.
+bool launch_magnetization(bool fp64, int which, int n, const void *X, void *Y, long long N, int r, int nsm,
+                          cudaStream_t st, int *status);
 
 
 // Observable Grams of V (N x r): blocks (column-major r x r each, complex double):
