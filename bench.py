@@ -31,6 +31,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+ERR_BOUND = 1e-6   # the metric's relative observable error bound
 METRIC = "RK4 steps/s at n=20,r=16: mixed+learned vs plain FP64 GPU at ≤1e-6 obs err"
 WORKLOAD = "open chain n=20 r=16 J=1 Bz=0.5 kappa=0.1 q-LL RK4 dt=0.01 Haar V Dirichlet(1) Lambda (seed 3000)"
 
@@ -366,7 +367,7 @@ def run_ours(args):
     learned_error = None
     if not args.no_learned:
         from paper_2508_21200_gb300 import controller as ctl
-        tol = max(args.tol, 5e-6)
+        tol = args.tol
         train_w = [li.workload(4, t, n=n, r=16, kappa=0.1) for t, n in ((1, 14), (2, 16), (3, 16), (4, 18), (5, 18))]
         t_tr = time.perf_counter()
         Xtr, Ytr = ctl.generate(train_w, t_end=0.6, tols=(1e-4, 3e-5, 1e-5, 5e-6), precision="mixed")
@@ -483,13 +484,19 @@ def run_ours(args):
 
     if rank != 0:
         return
-    head = value if learned is None else learned["equiv_steps_per_s"]
-    head_ms = ms_max if learned is None else learned["wall_ms"] / n_ad
+    # the learned leg is the headline only if it meets the metric's error bound
+    if learned is not None and not learned["obs_rel_err_vs_reference"] <= ERR_BOUND:
+        learned_error = (f"learned leg outside the observable error bound "
+                         f"({learned['obs_rel_err_vs_reference']:.3g} > {ERR_BOUND:g}); headline is the fixed-dt leg")
+        learned["within_bound"] = False
+    use_learned = learned is not None and learned.get("within_bound", True)
+    head = value if not use_learned else learned["equiv_steps_per_s"]
+    head_ms = ms_max if not use_learned else learned["wall_ms"] / n_ad
     out = {"metric": METRIC, "value": round(head, 3), "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
            "ms_per_step": round(head_ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64 bulk + f64 small solves", "data": "synthetic",
            "config": {"workload": WORKLOAD, "precision": "mixed_c64",
-                      "controller": ("fixed dt" if learned is None else
+                      "controller": ("fixed dt" if not use_learned else
                                      f"learned (value = dt=0.01-equivalent RK4 steps/s: (T/dt) / wall time of "
                                      f"the adaptive run from t=0 to T={T:g})"),
                       "parallelism": f"replicas x{world}",
@@ -500,7 +507,7 @@ def run_ours(args):
                         "obs_rel_err_vs_reference": obs_err(od)},
            "reference": "mixed path at dt/4 over the same span (observable errors are relative, floored scales)",
            "speedup_vs_fp64": round((head / (1000.0 / ms_fp64)), 2),
-           "learned": learned if learned_error is None else {"error": learned_error},
+           "learned": learned if learned_error is None else dict(learned or {}, error=learned_error),
            "obs_rel_err_vs_fp64": err, "ritz_rel_err_vs_fp64": err_mu,
            "roofline": roof, "roofline_hv": roof_hv,
            # the step against its HBM floor: each of the 4 stages reads the factor and writes W,
@@ -616,7 +623,7 @@ def run_workload5(args):
     Xtr, Ytr = ctl.generate(train_w, t_end=0.4, tols=(1e-4, 3e-5, 1e-5), precision="mixed")
     net, tr_loss = ctl.fit(Xtr, Ytr, iters=2000, lr=2e-3)
     t_tr = time.perf_counter() - t_tr
-    tol = max(args.tol, 5e-6)
+    tol = args.tol
 
     def adaptive(controller):
         L = make("mixed")
@@ -697,7 +704,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--tol", type=float, default=3e-6,
+                    help="adaptive legs: local error per step (the largest that keeps the n=20 run over "
+                         "[0, 1] within the 1e-6 observable bound, measured)")
     ap.add_argument("--t-adaptive", type=float, default=1.0, help="end of the adaptive window [0, T]")
     ap.add_argument("--judge-every", type=int, default=8)
     ap.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)

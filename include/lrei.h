@@ -136,7 +136,7 @@ int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
  * the step size falls below 1e-12 * max(1, |t_end|) or 64 steps in a row
  * are rejected. */
 #define LREI_TOL_FLOOR_FP64 1e-13
-#define LREI_TOL_FLOOR_MIXED 5e-6
+#define LREI_TOL_FLOOR_MIXED 1e-6
 int lrei_step_adaptive(lrei_ctx *ctx, double t_end, double tol, int controller);
 
 /* Compute observables of the current state into a host struct (syncs). */

@@ -70,7 +70,7 @@ def test_learned_controller_with_untrained_network_stays_safe():
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_tolerance_below_rounding_floor_terminates(precision):
     # a tolerance below what the stored factor can resolve is raised to the precision's floor
-    # (1e-13 FP64, 5e-6 complex64) instead of shrinking the step without end
+    # (1e-13 FP64, 1e-6 complex64) instead of shrinking the step without end
     w = li.workload(1, n=7, r=3)
     L = Lrei(w.n, w.bonds, w.B, w.kappa, w.model, precision, w.r)
     dt = torch.complex128 if precision == "fp64" else torch.complex64
