@@ -36,7 +36,8 @@ typedef struct lrei_ctx lrei_ctx; /* opaque; owns all device memory it uses */
 typedef enum {
   LREI_OK = 0,
   LREI_ERR_ARG = -1,         /* invalid argument (sizes, ranges, NULL) */
-  LREI_ERR_UNSUPPORTED = -2, /* valid request outside this build (an AB basis wider than 160) */
+  LREI_ERR_UNSUPPORTED = -2, /* valid request outside this build (an AB basis wider than 160,
+                              * the BF16-split precision) */
   LREI_ERR_NONFINITE = -3,   /* NaN/Inf in an input or produced by a step */
   LREI_ERR_TRACE = -4,       /* Lambda not >= 0 or |sum(Lambda) - 1| > 1e-12 */
   LREI_ERR_RANK = -5,        /* V rank-deficient */
@@ -58,8 +59,10 @@ typedef enum {
 /* Arithmetic of the N-length (bulk) work.  Small r x r / k x k solves are
  * FP64 in every mode. */
 typedef enum {
-  LREI_FP64 = 0,      /* complex128 storage and arithmetic */
-  LREI_MIXED_C64 = 1  /* complex64 storage and FP32 arithmetic, FP64 small solves */
+  LREI_FP64 = 0,        /* complex128 storage and arithmetic */
+  LREI_MIXED_C64 = 1,   /* complex64 storage and FP32 arithmetic, FP64 small solves */
+  LREI_MIXED_BF16X = 2  /* BF16-split tensor-core products: declared, not built in this version;
+                         * lrei_create returns LREI_ERR_UNSUPPORTED for it */
 } lrei_precision;
 
 typedef enum { LREI_C128 = 0, LREI_C64 = 1 } lrei_dtype;

@@ -18,7 +18,8 @@ from .build import LIB, ensure_built
 __all__ = ["Lrei", "Batch", "LreiError", "load_library", "QLL", "QLLG", "FP64", "MIXED_C64", "SCHEMES"]
 
 QLL, QLLG = 0, 1
-FP64, MIXED_C64 = 0, 1
+FP64, MIXED_C64, MIXED_BF16X = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "mixed": MIXED_C64, "bf16x": MIXED_BF16X}
 C128, C64 = 0, 1
 SCHEMES = {"rk1": 0, "rk2": 1, "rk3": 2, "rk4": 3, "ab2": 4, "ab3": 5, "ab4": 6}
 
@@ -98,6 +99,7 @@ def load_library(path: str | None = None):
         "lrei_householder": (I, [P, P, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "lrei_kernel_launches": (L, [P]),
         "lrei_last_status": (I, [P]),
+        "lrei_debug_counters": (I, [ctypes.POINTER(ctypes.c_ulonglong)]),
         "lrei_mlp_create": (I, [I, I, P, P, ctypes.POINTER(P)]),
         "lrei_mlp_destroy": (I, [P]),
         "lrei_mlp_num_params": (I, [P]),
@@ -140,7 +142,9 @@ class Lrei:
         lib = load_library()
         self._lib = lib
         self.n, self.N, self.r_max = n, 1 << n, r_max
-        self.precision = FP64 if precision == "fp64" else MIXED_C64
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        self.precision = PRECISIONS[precision]
         self._arrays = (np.ascontiguousarray(bonds.site_i, dtype=np.int32),
                         np.ascontiguousarray(bonds.site_j, dtype=np.int32),
                         np.ascontiguousarray(bonds.jxy, dtype=np.float64),
@@ -409,3 +413,12 @@ class Mlp:
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(self._lib.lrei_mlp_adam(self._h, lr, beta1, beta2, eps))
+
+
+def eig_counters():
+    """Cumulative small-eigensolver counters on the current device (lrei_debug_counters):
+    dict of FP32 Jacobi calls and sweeps, FP64 Jacobi calls and sweeps."""
+    lib = load_library()
+    out = (ctypes.c_ulonglong * 4)()
+    _check(lib.lrei_debug_counters(out))
+    return {"fp32_calls": out[0], "fp32_sweeps": out[1], "fp64_calls": out[2], "fp64_sweeps": out[3]}

@@ -1535,6 +1535,7 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   if (n < 1 || n > MAX_SPINS || r_max < 1 || r_max > MAX_R || !(lambda >= 0.0) || !std::isfinite(lambda))
     return LREI_ERR_ARG;
   if (model != LREI_QLL && model != LREI_QLLG) return LREI_ERR_ARG;
+  if (prec == LREI_MIXED_BF16X) return LREI_ERR_UNSUPPORTED;
   if (prec != LREI_FP64 && prec != LREI_MIXED_C64) return LREI_ERR_ARG;
   if ((long long)r_max > (1LL << n)) return LREI_ERR_ARG;
   ModelArgs Mk;

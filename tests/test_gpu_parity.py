@@ -260,6 +260,9 @@ def test_error_codes():
     with pytest.raises(LreiError) as e:
         L.set_dmi(np.zeros(len(w.bonds) + 1))
     assert e.value.code == -1                      # one DM vector per bond
+    with pytest.raises(LreiError) as e:
+        Lrei(w.n, w.bonds, w.B, 0.1, "qll", "bf16x", 2)
+    assert e.value.code == -2                      # the BF16-split precision is declared, not built
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -474,3 +477,19 @@ def test_eigensolver_sweep_limit_reports_no_convergence():
     L.step(w.dt, "rk4", 1)                       # the context stays usable
     with pytest.raises(LreiError):
         L.set_eig_sweeps(0)
+
+
+def test_eigensolver_counters_count_one_solve_per_stage():
+    # each RK4 stage diagonalises its stage matrix once: one FP32 Jacobi (all k eigenpairs) and one
+    # FP64 Jacobi (the r x r Rayleigh-Ritz), each taking at least one sweep
+    from paper_2508_21200_gb300 import eig_counters
+    w = li.workload(2, n=8, r=4)
+    L = ctx_for(w, "mixed")
+    L.set_state(dev(w.V, "mixed"), w.lam)
+    L.step(w.dt, "rk4", 1)            # the graph is built and run once
+    a = eig_counters()
+    L.step(w.dt, "rk4", 3)
+    b = eig_counters()
+    d = {k: b[k] - a[k] for k in a}
+    assert d["fp32_calls"] == 12 and d["fp64_calls"] == 12, d
+    assert d["fp32_sweeps"] >= 12 and d["fp64_sweeps"] >= 12, d

@@ -65,6 +65,25 @@ def test_noalloc_observables_match_context_observables_twice(precision, dtype, t
         assert got["r"] == w.r and np.allclose(got["lambda0"], lam)
 
 
+@pytest.mark.parametrize("precision,dtype,tol", [("fp64", 0, 1e-12), ("mixed", 1, 1e-6)])
+def test_noalloc_observables_match_the_dense_oracle(precision, dtype, tol):
+    # directly against the oracle's observables of rho = V Lambda V^* (dense, n = 8)
+    from oracle import model, dense_ei as de
+    lib = load_library()
+    w = li.workload(2, n=8, r=5)
+    V = torch.from_numpy(w.V).to("cuda", torch.complex128 if precision == "fp64" else torch.complex64)
+    got = _noalloc(lib, w, V, w.lam, dtype)
+    H = model.hamiltonian(w.n, w.bonds, w.B)
+    M = {v: model.magnetization_op(v, w.n) for v in "xyz"}
+    Vr = V.cpu().numpy().astype(np.complex128)   # the factor as stored (complex64 rounding included)
+    Rc = np.linalg.cholesky(Vr.conj().T @ Vr).conj().T
+    ref = de.observables(Vr @ np.linalg.inv(Rc), w.lam, H, M)
+    sE = float(np.sum(np.abs(w.bonds.jxy) + np.abs(w.bonds.jz) / 2) + w.n * np.linalg.norm(w.B) / 2)
+    for k, s in (("energy", sE), ("mx", 0.5), ("my", 0.5), ("mz", 0.5), ("purity", 1.0)):
+        assert abs(got[k] - ref[k]) <= tol * max(abs(ref[k]), s), (k, got[k], ref[k])
+    assert abs(got["comm_norm"] - ref["comm_norm"]) <= tol * max(ref["comm_norm"], 1.0)
+
+
 def test_noalloc_rejects_rank_above_its_limit():
     lib = load_library()
     w = li.workload(2, n=8, r=17, with_state=False)
