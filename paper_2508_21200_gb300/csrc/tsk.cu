@@ -501,8 +501,9 @@ __global__ void __launch_bounds__(TS_THREADS) ts2_kernel(const __grid_constant__
 // RS = r + 2 complex, so that rows of one column fall in different banks) while the current
 // tile is computed.  Gram work split: a micro-tile is column c of every Gram block against 4
 // consecutive G columns (g x 4 complex accumulators); NPH lanes of one warp take interleaved
-// rows of the same micro-tile and are combined by shuffles at each flush, every FLUSHT tiles,
-// into compensated FP32 pairs (TwoSum) in shared memory.  Lane = phase * TPW + micro-tile, so
+// rows of the same micro-tile and are combined by shuffles at each flush, every FLUSHT tiles
+// (at r = 16: 16 tiles, 128 rows per lane in plain FP32), into compensated FP32 pairs (TwoSum)
+// in shared memory.  Lane = phase * TPW + micro-tile, so
 // the G loads of a quarter-warp are one row (distinct 16-byte columns) and the block loads of
 // a half-warp are two rows of two columns: no bank conflicts at r = 16.
 template <int R, int TR, int GMAX, int MINB = (TR <= 32 ? 2 : 1)>
@@ -513,7 +514,12 @@ __global__ void __launch_bounds__(256, MINB) ts3_kernel(const __grid_constant__ 
   constexpr int NPH = 256 / MTS;
   constexpr int TPW = 32 / NPH;
   constexpr int CH = R / 2;                 // 16-byte chunks per row
-  constexpr int FLUSHT = 8;                 // GMAX: Gram blocks this instance handles (gl + 1 <= GMAX)
+  // GMAX: Gram blocks this instance handles (gl + 1 <= GMAX).  Flush period and row-loop unroll
+  // measured at n = 20, r = 16 (16 tiles and 8 / 4 for g = 2 / 5: 7-9% faster than 8 tiles and
+  // 2); the other widths keep the previous 8 and 2
+  constexpr int FLUSHT = R == 16 ? 16 : 8;
+  constexpr int UNR = R == 16 ? (GMAX <= 2 ? 8 : 4) : 2;
+  constexpr int PU = R == 16 ? 16 : 4;      // projection: inputs per block unrolled (measured, r = 16)
   static_assert(NPH >= 1 && NPH <= 32 && (32 % NPH) == 0 && (RS * 8) % 16 == 0, "r in {8, 16, 32}");
   extern __shared__ __align__(16) unsigned char smem3[];
   const int nq = a.nq, gl = a.gram_left, mode = a.mode;
@@ -605,7 +611,7 @@ __global__ void __launch_bounds__(256, MINB) ts3_kernel(const __grid_constant__ 
         for (int m = 0; m <= mlast; ++m) {
           const cx<float> *X = B0 + (size_t)m * bstride + lr * RS;
           const cx<float> *C = cs + (size_t)m * R * R + q0;
-#pragma unroll 4
+#pragma unroll PU
           for (int i = 0; i < R; ++i) {
             const cx<float> x = X[i];
             const float4 c01 = *reinterpret_cast<const float4 *>(C + i * R);
@@ -634,7 +640,7 @@ __global__ void __launch_bounds__(256, MINB) ts3_kernel(const __grid_constant__ 
     } else {
       G = B0 + (size_t)nq * bstride;
     }
-#pragma unroll 2
+#pragma unroll UNR
     for (int lr = ph; lr < TR; lr += NPH) {
       const float4 ga = *reinterpret_cast<const float4 *>(G + lr * RS + j0);
       const float4 gb = *reinterpret_cast<const float4 *>(G + lr * RS + j0 + 2);
