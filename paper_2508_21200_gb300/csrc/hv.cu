@@ -35,17 +35,6 @@ template <typename T> struct W16;
 template <> struct W16<float> { using V = float4; };
 template <> struct W16<double> { using V = double2; };
 
-__device__ __forceinline__ float4 ld_stream(const float4 *p) {
-  float4 v;
-  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ double2 ld_stream(const double2 *p) {
-  double2 v;
-  asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
-  return v;
-}
 __device__ __forceinline__ void axpy(float4 &a, float s, const float4 &p) {
   a.x = fmaf(s, p.x, a.x); a.y = fmaf(s, p.y, a.y); a.z = fmaf(s, p.z, a.z); a.w = fmaf(s, p.w, a.w);
 }
@@ -64,18 +53,6 @@ __device__ __forceinline__ float4 zero16(float4 *) { return make_float4(0.f, 0.f
 __device__ __forceinline__ double2 zero16(double2 *) { return make_double2(0.0, 0.0); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Bounded wait for phase `parity` of an mbarrier: 2^22 polls with back-off (a few hundred ms).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    uint32_t done;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    if (done) return true;
-    if (it > 32) __nanosleep(64);
-  }
-  return false;
-}
 
 }  // namespace
 

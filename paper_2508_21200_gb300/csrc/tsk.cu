@@ -21,10 +21,6 @@
 namespace lrei {
 
 // ---------------------------------------------------------------- loads
-template <typename T> struct VecT;
-template <> struct VecT<float> { using v2 = float2; using v4 = float4; };
-template <> struct VecT<double> { using v2 = double2; using v4 = double4; };
-
 __device__ __forceinline__ cx<float> ldg1(const cx<float> *p) {
   float2 v = __ldg(reinterpret_cast<const float2 *>(p));
   return mk<float>(v.x, v.y);
