@@ -88,8 +88,8 @@ struct HvPlan {
 // registers across its chunks and store them once.  Every wait is bounded: a consumer or the
 // producer that gives up sets ST_TIMEOUT and a shared abort flag that ends everyone's loop, and
 // the producer waits (bounded) for each buffer's last copy before the CTA exits.
-template <typename T, int NB, int RPT, bool CPLX, int MINB, int SUSP = 0>
-__global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ HvPlan P,
+template <typename T, int NB, int RPT, bool CPLX, int MINB, int SUSP = 0, int NCW = 8>
+__global__ void __launch_bounds__(NCW * 32 + 32, MINB) hv7_kernel(const __grid_constant__ HvPlan P,
                                                   const typename W16<T>::V *__restrict__ X,
                                                   typename W16<T>::V *__restrict__ Y, int *status) {
   using V = typename W16<T>::V;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
     abort_flag = 0;
     for (int i = 0; i < NB; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" ::"r"(smem_u32(&empty[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&empty[i])), "r"(NCW));
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
     return false;
   };
 
-  if (tid >= 256) {
+  if (tid >= NCW * 32) {
     // ---- producer warp: lane 0 issues every copy of the CTA's chunk sequence
-    if (tid != 256) return;
+    if (tid != NCW * 32) return;
     int last_u[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) last_u[i] = -1;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(288, MINB) hv7_kernel(const __grid_constant__ 
   }
 
   // ---- consumer warps: thread (slot, c) owns word c of rows slot + i rp of every tile
-  const int rp = 256 / ch;
+  const int rp = NCW * 32 / ch;
   const int slot = tid / ch, c = tid - slot * ch;
   const bool active_thread = slot < rp;
   const int lane = tid & 31;
