@@ -142,7 +142,11 @@ int lrei_step(lrei_ctx *ctx, double dt, lrei_scheme scheme, int nsteps);
 #define LREI_TOL_FLOOR_MIXED 1e-6
 int lrei_step_adaptive(lrei_ctx *ctx, double t_end, double tol, int controller);
 
-/* Compute observables of the current state into a host struct (syncs). */
+/* Compute observables of the current state into a host struct (Sec. 3.6: Tr(A rho) for
+ * A = H, M_x, M_y, M_z; Tr rho, Tr rho^2, ||[rho, H]||_F; the Ritz values of the last step and
+ * the conserved spectrum; ||V^*V - I|| and the Hermiticity error of V^*HV as diagnostics).
+ * Uses the context's step buffers as scratch (no allocation) and syncs the context's stream.
+ * Returns LREI_ERR_STATE before set_state. */
 int lrei_observables(lrei_ctx *ctx, lrei_obs *out);
 
 /* Dzyaloshinskii-Moriya vectors along z (eq. H1: 2 d_ij . (S_i x S_j) with d_ij = dz[b] e_z for
