@@ -1569,10 +1569,11 @@ int lrei_create(int n, const lrei_bonds *J, const double B[3], double lambda, lr
   cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   for (int i = 0; i < 4; ++i) cudaEventCreateWithFlags(&c->ev_kry[i], cudaEventDisableTiming);
   c->nsm_use = c->nsm;
-  // the complex64 N-length passes of the RK step leave one SM in sixteen to the stage algebra
-  // running beside them; the FP64 passes are long enough that the stage algebra hides behind
-  // them without a reserve
-  c->nsm_pass = c->fp64 ? c->nsm_use : c->nsm_use - std::max(1, c->nsm_use / 16);
+  // the complex64 N-length passes of the RK step leave one SM in 32 to the stage algebra running
+  // beside them (measured at n=20, r=16: 5.55 ms per step against 5.61 with one in 16, 5.88 with
+  // one in 8 and 6.25 with none); the FP64 passes are long enough that the stage algebra hides
+  // behind them without a reserve
+  c->nsm_pass = c->fp64 ? c->nsm_use : c->nsm_use - std::max(1, c->nsm_use / 32);
   if (ts_init() || sm_init()) return fail(LREI_ERR_CUDA);
   {
     const int lim = 100 * 1024;
